@@ -1,0 +1,477 @@
+"""FP64 CPU oracle of live Wigner Distribution Deconvolution (WDD), written from the paper.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module.  It shares no code with the CUDA library.
+
+Everything is float64 / complex128 numpy.  Library routines (numpy FFT, matmul) serve as single
+steps; there is no blocking or reordering beyond what each cited equation or algorithm states.
+
+Notation (Sect. 2): scan S = S_y x S_x positions s = s_y*S_x + s_x at r_s = (s_y, s_x) * step;
+scan frequencies v = v_y*S_x + v_x; detector N_y x N_x pixels, frames stored with zero frequency
+at pixel (c_y, c_x); K reduced coefficients per frame.
+
+Readings of the paper (each one is also listed in the design notes):
+  R1 Bases.  "fourier_full": real cos/sin rows of the detector inverse DFT (K = N_y*N_x), which
+     makes the live method reproduce classical WDD exactly.  "hg_tensor": the operator H of
+     Sect. 5 with L x L Hermite-Gauss functions.  "hg_energy": the first K tensor pairs ordered
+     by the 2-D oscillator energy n_y + n_x (Eq. 10), ties by smaller n_y.
+  R2 The reduced-space deconvolution is the element-wise product of Algorithm 1 and 2.
+  R3 The 2-D eigenfunction is the tensor product of 1-D functions with sigma applied once.
+  R4 Hermite-Gauss columns are built by the normalised three-term recurrence and rescaled to unit
+     discrete L2 norm; sigma = R_bf / sqrt(2*(L-1)+1) with R_bf the bright-field radius in
+     pixels, sampled at x_j = j - c (c = detector centre, not estimated from data).
+  R5 epsilon is relative: eps_eff = epsilon * max_{v,m} |chi_v[m]|^2 (an absolute mode exists).
+  R6 Eq. 3's division by sqrt(o_0) is applied (principal root; skipped when o_0 == 0), then the
+     conjugated inverse DFT of Algorithm 2 with numpy's 1/S normalisation.
+  R7 Sum of all elements of D_v is the zero-frequency extraction, used literally.
+  R8 A frequency is active iff the two aperture discs overlap: |q_v| < 2 theta / lambda (strict).
+  R9 Sign conventions: P_s = p(r - r_s); scan kernel exp(-2 pi i q_v . r_s); Y_v(q) =
+     p(q) conj p(q + q_v); probe p(k) = [|k| <= theta/lambda] exp(-i pi lambda df |k|^2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "electron_wavelength", "overlap_bound_ratio", "Params", "signed_freq", "scan_shift_px",
+    "bright_field_radius_px", "probe_spectrum", "probe_autocorrelation", "hg_functions_1d",
+    "energy_pairs", "hg_energy_l", "OraclePlan", "build_plan", "project_operator",
+    "coefficients", "phase_factor", "accumulate", "deconvolve", "finalize", "live_wdd",
+    "live_wdd_per_frame", "offline_wdd", "phase_rel_l2", "complex_rel_l2", "active_mask",
+    "fourier_window_plan",
+]
+
+# CODATA 2018 constants (SI).
+PLANCK = 6.62607015e-34
+ELECTRON_MASS = 9.1093837015e-31
+ELEMENTARY_CHARGE = 1.602176634e-19
+SPEED_OF_LIGHT = 299792458.0
+
+
+# ---------------------------------------------------------------------------------------------
+# Acquisition geometry (Sect. 6.3, Eq. 12-14)
+# ---------------------------------------------------------------------------------------------
+
+def electron_wavelength(voltage_v: float) -> float:
+    """Relativistic de Broglie wavelength lambda(V) in metres.
+
+    lambda = h / sqrt(2 m0 e V (1 + e V / (2 m0 c^2))).  Evaluated as a fixed sequence of
+    correctly rounded IEEE operations.  Pinned by the 200 kV value 2.508 pm quoted in Sect. 6.3.
+    """
+    ev = ELEMENTARY_CHARGE * voltage_v
+    rel = 1.0 + ev / (2.0 * ELECTRON_MASS * SPEED_OF_LIGHT * SPEED_OF_LIGHT)
+    return PLANCK / math.sqrt(2.0 * ELECTRON_MASS * ev * rel)
+
+
+def overlap_bound_ratio(step_m: float, semiconv_rad: float, wavelength_m: float) -> float:
+    """S_hat / S = sqrt(2) * Delta * sin(theta) / lambda (Eq. 14).  Pinned by the 0.47 example."""
+    return math.sqrt(2.0) * step_m * math.sin(semiconv_rad) / wavelength_m
+
+
+@dataclasses.dataclass
+class Params:
+    """Acquisition and reconstruction parameters (the problem statement of Sect. 2)."""
+    scan_y: int
+    scan_x: int
+    scan_step_m: float
+    det_y: int
+    det_x: int
+    det_px_inv_m: float
+    voltage_v: float
+    semiconv_rad: float
+    defocus_m: float
+    epsilon: float
+    rank_k: int
+    basis: str = "hg_tensor"          # "fourier_full" | "hg_tensor" | "hg_energy"
+    det_center_y: float | None = None  # default det_y // 2
+    det_center_x: float | None = None
+    eps_absolute: bool = False
+
+    @property
+    def S(self) -> int:
+        return self.scan_y * self.scan_x
+
+    @property
+    def cy(self) -> float:
+        return float(self.det_y // 2) if self.det_center_y is None else float(self.det_center_y)
+
+    @property
+    def cx(self) -> float:
+        return float(self.det_x // 2) if self.det_center_x is None else float(self.det_center_x)
+
+    @property
+    def wavelength_m(self) -> float:
+        return electron_wavelength(self.voltage_v)
+
+    @staticmethod
+    def from_acquisition(acq, basis: str, rank_k: int, epsilon: float, **kw) -> "Params":
+        return Params(scan_y=acq.scan_y, scan_x=acq.scan_x, scan_step_m=acq.scan_step_m,
+                      det_y=acq.det, det_x=acq.det, det_px_inv_m=acq.det_px_inv_m,
+                      voltage_v=acq.voltage_v, semiconv_rad=acq.semiconv_rad,
+                      defocus_m=acq.defocus_m, epsilon=epsilon, rank_k=rank_k, basis=basis, **kw)
+
+
+def signed_freq(v: np.ndarray | int, n: int):
+    """Signed DFT frequency index of bin v (numpy fftfreq ordering times n)."""
+    v = np.asarray(v)
+    return np.where(v <= (n - 1) // 2, v, v - n)
+
+
+def scan_shift_px(p: Params) -> tuple[np.ndarray, np.ndarray]:
+    """Detector-pixel shift q_v / dk of every scan frequency, per axis (Eq. 13 geometry).
+
+    q_v = (f_y / (S_y * Delta), f_x / (S_x * Delta)) in reciprocal metres with signed
+    frequencies f; dividing by the detector sampling dk gives pixels.
+    """
+    fy = signed_freq(np.arange(p.scan_y), p.scan_y).astype(np.float64)
+    fx = signed_freq(np.arange(p.scan_x), p.scan_x).astype(np.float64)
+    qy = fy / (p.scan_y * p.scan_step_m * p.det_px_inv_m)
+    qx = fx / (p.scan_x * p.scan_step_m * p.det_px_inv_m)
+    return qy, qx
+
+
+def bright_field_radius_px(p: Params) -> float:
+    """Aperture radius theta / (lambda dk) in detector pixels."""
+    return p.semiconv_rad / (p.wavelength_m * p.det_px_inv_m)
+
+
+def active_mask(p: Params) -> np.ndarray:
+    """Frequencies whose shifted aperture discs intersect: |q_v| < 2 R (reading R8, Eq. 12)."""
+    qy, qx = scan_shift_px(p)
+    r = bright_field_radius_px(p)
+    d2 = qy[:, None] * qy[:, None] + qx[None, :] * qx[None, :]
+    return (d2 < 4.0 * (r * r)).reshape(-1)
+
+
+# ---------------------------------------------------------------------------------------------
+# Probe and its autocorrelation (Eq. 2, Algorithm 1)
+# ---------------------------------------------------------------------------------------------
+
+def probe_spectrum(ky_px: np.ndarray, kx_px: np.ndarray, p: Params) -> np.ndarray:
+    """Probe in reciprocal space, evaluated analytically at (possibly sub-pixel) points.
+
+    p(k) = [|k|^2 <= R^2] * exp(-i pi lambda df dk^2 |k|^2), k in detector pixels, R the
+    bright-field radius (Algorithm 1 initialisation: circular aperture).
+    """
+    r = bright_field_radius_px(p)
+    k2 = ky_px * ky_px + kx_px * kx_px
+    amp = (k2 <= r * r).astype(np.float64)
+    lam = p.wavelength_m
+    dk = p.det_px_inv_m
+    coef = math.pi * lam * p.defocus_m * (dk * dk)
+    return amp * np.exp(-1j * (coef * k2))
+
+
+def probe_autocorrelation(p: Params, vy: int, vx: int) -> np.ndarray:
+    """Y_v(q) = p(q) * conj p(q + q_v) on the detector grid (Algorithm 1, Eq. 2 W_P)."""
+    qy_all, qx_all = scan_shift_px(p)
+    qy = np.arange(p.det_y, dtype=np.float64) - p.cy
+    qx = np.arange(p.det_x, dtype=np.float64) - p.cx
+    ky, kx = np.meshgrid(qy, qx, indexing="ij")
+    a = probe_spectrum(ky, kx, p)
+    b = probe_spectrum(ky + qy_all[vy], kx + qx_all[vx], p)
+    return a * np.conj(b)
+
+
+# ---------------------------------------------------------------------------------------------
+# Hermite-Gauss basis (Sect. 4, Sect. 5)
+# ---------------------------------------------------------------------------------------------
+
+def hg_functions_1d(n_pts: int, L: int, sigma: float, center: float) -> np.ndarray:
+    """Sampled 1-D oscillator eigenfunctions psi_0..psi_{L-1} (Eq. 5), shape (n_pts, L).
+
+    psi_n(x) is proportional to H_n(x / sigma) exp(-x^2 / (2 sigma^2)); the normalised three-term
+    recurrence avoids overflowing H_n.  Each column is then scaled to unit discrete L2 norm
+    (reading R4).  Pinned against numpy's Hermite polynomial evaluation and the oscillator
+    eigen-energies of Eq. 4.
+    """
+    x = (np.arange(n_pts, dtype=np.float64) - center) / sigma
+    out = np.zeros((n_pts, L), dtype=np.float64)
+    out[:, 0] = math.pi ** -0.25 * np.exp(-0.5 * x * x)
+    if L > 1:
+        out[:, 1] = math.sqrt(2.0) * x * out[:, 0]
+    for n in range(1, L - 1):
+        out[:, n + 1] = math.sqrt(2.0 / (n + 1)) * x * out[:, n] - math.sqrt(n / (n + 1.0)) * out[:, n - 1]
+    norms = np.sqrt((out * out).sum(axis=0))
+    norms[norms == 0] = 1.0
+    return out / norms
+
+
+def energy_pairs(K: int) -> list[tuple[int, int]]:
+    """First K index pairs (n_y, n_x) by 2-D oscillator energy n_y + n_x (Eq. 10), ties by n_y."""
+    pairs = []
+    e = 0
+    while len(pairs) < K:
+        for ny in range(e + 1):
+            pairs.append((ny, e - ny))
+            if len(pairs) == K:
+                break
+        e += 1
+    return pairs
+
+
+def hg_energy_l(K: int) -> int:
+    """Number of 1-D functions the first K energy-ordered pairs need."""
+    return 1 + max(max(a, b) for a, b in energy_pairs(K))
+
+
+# ---------------------------------------------------------------------------------------------
+# Plan: bases, coefficient table, pre-computed Wiener filter (Algorithm 1)
+# ---------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class OraclePlan:
+    params: Params
+    By: np.ndarray          # (N_y, L_y) basis along detector rows (real or complex)
+    Bx: np.ndarray          # (N_x, L_x)
+    m_idx: np.ndarray       # (K,) flat index ly*L_x + lx of each coefficient
+    comp: np.ndarray        # (K,) 0 = real part, 1 = imaginary part
+    m_neg: np.ndarray       # (K,) flat index of -r (Fourier rows only; else = m_idx)
+    chi: np.ndarray         # (S, M) complex projected probe autocorrelation, M = L_y * L_x
+    W: np.ndarray           # (S, K) complex Wiener weights (zero on inactive v)
+    mask: np.ndarray        # (S,) bool active frequencies
+    eps_eff: float
+
+    @property
+    def K(self) -> int:
+        return int(self.m_idx.shape[0])
+
+
+def project_operator(A: np.ndarray, By: np.ndarray, Bx: np.ndarray) -> np.ndarray:
+    """The reduction operator H of Sect. 5 on one detector image: Z = By^T A Bx.
+
+    Z[ly, lx] = sum_{i,j} By[i, ly] A[i, j] Bx[j, lx].  (Sect. 5 writes psi_x^T A^T psi_y, the
+    transpose of the same matrix; data and probe pass through the same map, so the orientation
+    only relabels coefficients.)
+    """
+    return By.T @ A @ Bx
+
+
+def _fourier_tables(ny: int, nx: int):
+    m_idx, comp, m_neg = [], [], []
+    for ry in range(ny):
+        for rx in range(nx):
+            m = ry * nx + rx
+            n = ((-ry) % ny) * nx + ((-rx) % nx)
+            if m > n:
+                continue
+            m_idx.append(m); comp.append(0); m_neg.append(n)
+            if m != n:
+                m_idx.append(m); comp.append(1); m_neg.append(n)
+    return np.array(m_idx), np.array(comp), np.array(m_neg)
+
+
+def _bases(p: Params):
+    """Basis matrices and coefficient table for the chosen family (reading R1)."""
+    if p.basis == "fourier_full":
+        ry = np.arange(p.det_y)
+        rx = np.arange(p.det_x)
+        qy = np.arange(p.det_y, dtype=np.float64) - p.cy
+        qx = np.arange(p.det_x, dtype=np.float64) - p.cx
+        By = np.exp(2j * np.pi * np.outer(qy, ry) / p.det_y) / p.det_y
+        Bx = np.exp(2j * np.pi * np.outer(qx, rx) / p.det_x) / p.det_x
+        m_idx, comp, m_neg = _fourier_tables(p.det_y, p.det_x)
+        if p.rank_k != m_idx.shape[0]:
+            raise ValueError("fourier_full needs rank_k = det_y * det_x")
+        return By, Bx, m_idx, comp, m_neg
+    r = bright_field_radius_px(p)
+    if p.basis == "hg_tensor":
+        L = int(round(math.sqrt(p.rank_k)))
+        if L * L != p.rank_k:
+            raise ValueError("hg_tensor needs a square rank_k")
+        pairs = [(a, b) for a in range(L) for b in range(L)]
+    elif p.basis == "hg_energy":
+        L = hg_energy_l(p.rank_k)
+        pairs = energy_pairs(p.rank_k)
+    else:
+        raise ValueError(p.basis)
+    sigma = r / math.sqrt(2.0 * (L - 1) + 1.0)
+    By = hg_functions_1d(p.det_y, L, sigma, p.cy)
+    Bx = hg_functions_1d(p.det_x, L, sigma, p.cx)
+    m_idx = np.array([a * L + b for a, b in pairs])
+    comp = np.zeros_like(m_idx)
+    return By, Bx, m_idx, comp, m_idx.copy()
+
+
+def build_plan(p: Params) -> OraclePlan:
+    """Algorithm 1: for every scan frequency v build Y_v, reduce it, form the Wiener filter.
+
+    chi_v = H(Y_v) (complex), K_v = conj(chi_v) / (|chi_v|^2 + eps_eff), then the weights W_v[k]
+    that multiply the real data coefficients: for the Hermite-Gauss families W_v[k] = K_v[m_k];
+    for the Fourier family the cos/sin rows of r and -r are paired,
+        W[cos r] = K(r) + K(-r)   (K(r) alone when r = -r),   W[sin r] = i (K(r) - K(-r)),
+    which is the same sum over all r written with real coefficients.  Inactive v get W_v = 0.
+    """
+    By, Bx, m_idx, comp, m_neg = _bases(p)
+    M = By.shape[1] * Bx.shape[1]
+    chi = np.zeros((p.S, M), dtype=np.complex128)
+    for vy in range(p.scan_y):
+        for vx in range(p.scan_x):
+            Y = probe_autocorrelation(p, vy, vx)
+            chi[vy * p.scan_x + vx] = project_operator(Y, By, Bx).reshape(-1)
+    used = np.unique(np.concatenate([m_idx, m_neg]))
+    if p.eps_absolute:
+        eps_eff = p.epsilon
+    else:
+        eps_eff = p.epsilon * float(np.max(np.abs(chi[:, used]) ** 2))
+    Kv = np.conj(chi) / (np.abs(chi) ** 2 + eps_eff)
+    if p.basis == "fourier_full":
+        self_conj = m_idx == m_neg
+        Kr = Kv[:, m_idx]
+        Kn = Kv[:, m_neg]
+        W = np.where(comp[None, :] == 0, np.where(self_conj[None, :], Kr, Kr + Kn), 1j * (Kr - Kn))
+    else:
+        W = Kv[:, m_idx]
+    mask = active_mask(p)
+    W = np.where(mask[:, None], W, 0.0)
+    return OraclePlan(params=p, By=By, Bx=Bx, m_idx=m_idx, comp=comp, m_neg=m_neg, chi=chi,
+                      W=W, mask=mask, eps_eff=eps_eff)
+
+
+def fourier_window_plan(p: Params, keep_k: int) -> OraclePlan:
+    """Fourier family reduced to the keep_k coefficients of smallest |r| (reduced-rank check)."""
+    full = build_plan(dataclasses.replace(p, basis="fourier_full", rank_k=p.det_y * p.det_x))
+    Lx = p.det_x
+    ry = full.m_idx // Lx
+    rx = full.m_idx % Lx
+    fy = signed_freq(ry, p.det_y)
+    fx = signed_freq(rx, p.det_x)
+    order = np.lexsort((np.arange(full.K), fy * fy + fx * fx))[:keep_k]
+    order = np.sort(order)
+    return dataclasses.replace(full, m_idx=full.m_idx[order], comp=full.comp[order],
+                               m_neg=full.m_neg[order], W=full.W[:, order])
+
+
+# ---------------------------------------------------------------------------------------------
+# Streaming path (Algorithm 2, Eq. outer_prod)
+# ---------------------------------------------------------------------------------------------
+
+def coefficients(frames: np.ndarray, plan: OraclePlan) -> np.ndarray:
+    """Algorithm 2 step 1: c_s = vec(H(I_s)) as K real coefficients, shape (n, K)."""
+    f = np.asarray(frames, dtype=np.float64)
+    Z = np.einsum("iy,nij,jx->nyx", plan.By, f, plan.Bx, optimize=True)
+    Z = Z.reshape(f.shape[0], -1)[:, plan.m_idx]
+    return np.where(plan.comp[None, :] == 0, Z.real, Z.imag)
+
+
+def phase_factor(p: Params, v: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """F_2D entries exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x)) from the two 1-D DFT matrices.
+
+    Returns the (len(v), len(s)) sub-matrix (Algorithm 2: subset of F_2D for the frames at hand).
+    """
+    v = np.asarray(v, dtype=np.int64)
+    s = np.asarray(s, dtype=np.int64)
+    vy, vx = v // p.scan_x, v % p.scan_x
+    sy, sx = s // p.scan_x, s % p.scan_x
+    Fy = np.exp(-2j * np.pi * np.outer(vy, sy) / p.scan_y)
+    Fx = np.exp(-2j * np.pi * np.outer(vx, sx) / p.scan_x)
+    return Fy * Fx
+
+
+def accumulate(C: np.ndarray, scan_idx: np.ndarray, p: Params,
+               v_rows: np.ndarray | None = None, chunk: int = 2048) -> np.ndarray:
+    """H[v, k] = sum_s F_2D[v, s] c_s[k]: Eq. outer_prod as one matrix product per row block.
+
+    Returns H for the requested rows (all S by default), complex (len(v_rows), K).
+    """
+    if v_rows is None:
+        v_rows = np.arange(p.S)
+    C = np.asarray(C, dtype=np.float64)
+    H = np.zeros((len(v_rows), C.shape[1]), dtype=np.complex128)
+    for a in range(0, len(v_rows), chunk):
+        E = phase_factor(p, v_rows[a:a + chunk], scan_idx)
+        H[a:a + chunk] = E @ C
+    return H
+
+
+def deconvolve(H: np.ndarray, plan: OraclePlan, v_rows: np.ndarray | None = None) -> np.ndarray:
+    """Algorithm 2: D_v = t_v o K_v, o_v = sum of all elements of D_v (reading R2, R7)."""
+    W = plan.W if v_rows is None else plan.W[v_rows]
+    return (W * H).sum(axis=1)
+
+
+def finalize(o: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
+    """Eq. 3 normalisation by sqrt(o_0), then conj(F^-1(O)) of Algorithm 2 (reading R6).
+
+    Returns (complex object transfer function S_y x S_x, phase in radians).
+    """
+    o = np.asarray(o, dtype=np.complex128).reshape(p.scan_y, p.scan_x)
+    o0 = o[0, 0]
+    scale = 1.0 / np.sqrt(o0) if o0 != 0 else 1.0
+    obj = np.conj(np.fft.ifft2(o * scale))
+    return obj, np.angle(obj)
+
+
+def live_wdd(frames: np.ndarray, scan_idx: np.ndarray, plan: OraclePlan,
+             chunk: int = 4096) -> np.ndarray:
+    """Live WDD in batched matrix form: o = deconvolve(F_2D[:, s] @ C) over all frames."""
+    p = plan.params
+    C = np.concatenate([coefficients(frames[a:a + chunk], plan)
+                        for a in range(0, frames.shape[0], chunk)], axis=0)
+    H = accumulate(C, np.asarray(scan_idx), p)
+    return deconvolve(H, plan)
+
+
+def live_wdd_per_frame(frames: np.ndarray, scan_idx: np.ndarray, plan: OraclePlan) -> np.ndarray:
+    """Algorithm 2 frame by frame: T = f_s i_s^T, D_v = mat(t_v) o K_v, o_v = sum, O += o."""
+    p = plan.params
+    O = np.zeros(p.S, dtype=np.complex128)
+    allv = np.arange(p.S)
+    active = np.nonzero(plan.mask)[0]
+    for fr, s in zip(frames, scan_idx):
+        i_s = coefficients(fr[None], plan)[0]
+        f_s = phase_factor(p, allv, np.array([s]))[:, 0]
+        T = np.outer(f_s, i_s)
+        o = np.zeros(p.S, dtype=np.complex128)
+        o[active] = (T[active] * plan.W[active]).sum(axis=1)
+        O += o
+    return O
+
+
+# ---------------------------------------------------------------------------------------------
+# Classical (offline) WDD, Eq. 2 and Eq. 3
+# ---------------------------------------------------------------------------------------------
+
+def offline_wdd(frames: np.ndarray, p: Params) -> np.ndarray:
+    """Classical WDD on the whole 4-D dataset; returns the spectrum o (S complex).
+
+    G = F_rhat(I) (scan DFT), then per frequency: W_P = F_q^-1(Y_v), the data's F_q^-1(G_v),
+    W_O = F_q^-1(G_v) conj(W_P) / (|W_P|^2 + eps_eff), o_v = F_r(W_O)|_{q=0} = sum_r W_O.
+    Detector arrays are ifftshifted so their zero frequency sits at index 0 (this requires the
+    detector centre to be at N//2).  Inactive frequencies (reading R8) are zeroed.
+    """
+    if p.cy != p.det_y // 2 or p.cx != p.det_x // 2:
+        raise ValueError("offline WDD assumes the detector centre at N//2")
+    I4 = np.asarray(frames, dtype=np.float64).reshape(p.scan_y, p.scan_x, p.det_y, p.det_x)
+    G = np.fft.fft2(I4, axes=(0, 1))
+    WP = np.empty((p.scan_y, p.scan_x, p.det_y, p.det_x), dtype=np.complex128)
+    for vy in range(p.scan_y):
+        for vx in range(p.scan_x):
+            WP[vy, vx] = np.fft.ifft2(np.fft.ifftshift(probe_autocorrelation(p, vy, vx)))
+    eps_eff = p.epsilon if p.eps_absolute else p.epsilon * float(np.max(np.abs(WP) ** 2))
+    GP = np.fft.ifft2(np.fft.ifftshift(G, axes=(2, 3)), axes=(2, 3))
+    WO = GP * np.conj(WP) / (np.abs(WP) ** 2 + eps_eff)
+    o = WO.sum(axis=(2, 3)).reshape(-1)
+    return np.where(active_mask(p), o, 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Error metrics
+# ---------------------------------------------------------------------------------------------
+
+def phase_rel_l2(phi: np.ndarray, phi_ref: np.ndarray) -> float:
+    """Relative L2 distance of mean-subtracted phase maps."""
+    a = np.asarray(phi, dtype=np.float64)
+    b = np.asarray(phi_ref, dtype=np.float64)
+    a = a - a.mean()
+    b = b - b.mean()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def complex_rel_l2(x: np.ndarray, ref: np.ndarray) -> float:
+    x = np.asarray(x, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
