@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Live-WDD benchmark on GB300.
+
+One step = one full live acquisition of the workload: every frame of the 128 x 128 scan
+(128 x 128 float32 detector, Poisson 1e4 e-/frame, Hermite-Gauss K = 64) is pushed in 64-frame
+batches (projection + phase accumulation), then a snapshot runs the deconvolution and the inverse
+DFT.  `value` = frames reconstructed per second over all ranks, timed with CUDA events on the
+launch stream with the frames already resident in HBM (1.07 GB of frames per step, larger than
+L2).  The optimised path replays the step as one captured CUDA graph; the plain FP32 path
+(`baseline_fp32_plain`) runs the same steps eagerly with every push accumulated at once.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent acquisition (replicas, weak scaling, no
+collective on the data path); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2"
+METRIC = "live WDD frames/s and p99 frame latency vs plain FP32 path; % tensor peak"
+UNIT = "frames/s"
+LATENCY_SNAPSHOT_EVERY = 1024
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"],
+                    bf16_sust=d.get("bf16_tflops_sustained", d["bf16_tflops"]), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(acq, rc, frames, idx, n_sample: int):
+    """Times the oracle's live path (coefficients, accumulation over every scan frequency,
+    deconvolution, inverse DFT) on the first n_sample frames.  Returns (seconds, cores)."""
+    import oracle.wdd_oracle as W
+    p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                  epsilon=rc["epsilon"])
+    plan = W.build_plan(p)
+    t0 = time.perf_counter()
+    o = W.live_wdd(frames[:n_sample], idx[:n_sample], plan)
+    W.finalize(o, p)
+    return time.perf_counter() - t0, os.cpu_count()
+
+
+def run_reference(args):
+    import synth
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    acq, rc = synth.config(WORKLOAD)
+    n_sample = 1024
+    idx = synth.raster_indices(acq)
+    frames = np.concatenate([f for _, f in synth.frames(acq, 0, n_sample, chunk=1024)])
+    times = []
+    cores = os.cpu_count()
+    for it in range(args.warmup + args.steps):
+        dt, cores = oracle_sample(acq, rc, frames, idx, n_sample)
+        if it >= args.warmup:
+            times.append(dt)
+    sec = float(np.mean(times))
+    fps = n_sample / sec
+    sample = (f"{n_sample} of {acq.n_frames} frames of the workload per step (coefficients, "
+              "accumulation over all scan frequencies, deconvolution, inverse DFT); plan build "
+              "excluded")
+    out = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "128x128 scan, 128x128 f32 detector, HG K=64, B=64",
+                      "name": WORKLOAD},
+           "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["auto", "fp32", "split"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2212_01309_gb300 import wdd
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    acq, rc = synth.config(WORKLOAD)
+    B = rc["batch"]
+    frames = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    S = acq.n_frames
+    d_frames = torch.from_numpy(frames).cuda()
+    h_frames = torch.from_numpy(frames).pin_memory()
+    stream = torch.cuda.Stream()
+    obj = torch.empty((acq.scan_y, acq.scan_x), dtype=torch.complex64, device="cuda")
+    phase = torch.empty((acq.scan_y, acq.scan_x), dtype=torch.float32, device="cuda")
+    h_phase = torch.empty_like(phase, device="cpu").pin_memory()
+
+    split_ok = True
+    path = args.path
+    if path in ("auto", "split"):
+        try:
+            wdd.Plan(wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                                 precision="split", max_batch=B,
+                                                 accum_depth=1024)).close()
+        except wdd.WddError:
+            split_ok = False
+            if path == "split":
+                raise
+        path = "split" if split_ok else "fp32"
+
+    def mk(precision, depth):
+        return wdd.Plan(wdd.params_from_acquisition(
+            acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"],
+            precision=precision, max_batch=B, accum_depth=depth))
+
+    plain = mk("fp32", 0)
+    opt = mk(path, 1024)
+
+    def step(plan, src):
+        plan.reset(stream=stream)
+        for a in range(0, S, B):
+            plan.push(src[a:a + B], idx[a:a + B], stream=stream)
+        plan.snapshot(obj, phase, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        barrier()
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    with torch.cuda.stream(stream):
+        # ---- plain FP32 path (eager, every push accumulated at once) -------------------------
+        for _ in range(args.warmup):
+            step(plain, d_frames)
+        ms_plain = timed(lambda: step(plain, d_frames), args.steps)
+        _, ph_plain = obj.clone(), phase.clone()
+
+        # ---- optimised path: staged accumulation, one CUDA graph per acquisition -------------
+        for _ in range(args.warmup):
+            step(opt, d_frames)
+        torch.cuda.synchronize()
+        launches0 = opt.info()["kernel_launches"]
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step(opt, d_frames)
+        launches_per_step = opt.info()["kernel_launches"] - launches0
+        for _ in range(args.warmup):
+            graph.replay()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms_opt = timed(graph.replay, args.steps)
+        clk = clocks.stop()
+        ph_opt = phase.clone()
+
+        # ---- stage times of the optimised path (eager step, events on the launch stream) -----
+        opt.set_stage_timing(True)
+        step(opt, d_frames)
+        st = opt.stage_times()
+        opt.set_stage_timing(False)
+
+        # ---- end to end through the public API from pinned host memory ---------------------
+        def e2e_step():
+            step(opt, h_frames)
+            h_phase.copy_(phase, non_blocking=True)
+        for _ in range(2):
+            e2e_step()
+        ms_e2e = timed(e2e_step, max(2, args.steps // 2))
+
+        # ---- frame-to-snapshot latency (snapshot every 1024 frames) ------------------------
+        lat = []
+        opt.reset(stream=stream)
+        torch.cuda.synchronize()
+        pending = []
+        for a in range(0, S, B):
+            t_arr = time.perf_counter()
+            opt.push(d_frames[a:a + B], idx[a:a + B], stream=stream)
+            pending.append((t_arr, min(B, S - a)))
+            if (a + B) % LATENCY_SNAPSHOT_EVERY == 0 or a + B >= S:
+                opt.snapshot(obj, phase, stream=stream)
+                stream.synchronize()
+                t_done = time.perf_counter()
+                for t0, n in pending:
+                    lat.extend([t_done - t0] * n)
+                pending = []
+    torch.cuda.synchronize()
+
+    err = float(np.linalg.norm((ph_opt - ph_opt.mean()).cpu().numpy() -
+                               (ph_plain - ph_plain.mean()).cpu().numpy()) /
+                np.linalg.norm((ph_plain - ph_plain.mean()).cpu().numpy()))
+
+    # ---- roofline of the dominant kernel --------------------------------------------------
+    peaks = _peaks()
+    frames_bytes = acq.det * acq.det * np.dtype(acq.np_dtype).itemsize
+    K = rc["rank_k"]
+    stage_ms = {k: v[0] for k, v in st.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    ms_launch = st[dom][0] / max(1, st[dom][1])
+    if dom == "accumulate":
+        n_per = 1024 if path == "split" or opt.params.accum_depth else B
+        flops = 4.0 * S * K * n_per
+        ach = flops / (ms_launch * 1e-3) / 1e12
+        if path == "split":
+            roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["bf16"], "traffic": None,
+                    "note": f"algorithmic 4*S*K flops per frame; executed = 3x (split); peak "
+                            f"= {peaks['src']} bf16 dense (fp16 same rate)"}
+        else:
+            roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                    "note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+    elif dom == "project":
+        bpl = B * frames_bytes
+        ach = bpl / (ms_launch * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": ach / peaks["hbm"], "traffic": None}
+    else:
+        bpl = 16.0 * S * K
+        ach = bpl / (ms_launch * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": ach / peaks["hbm"], "traffic": None}
+    roof["kernel"] = dom
+    roof["launch_ms"] = ms_launch
+
+    # ---- CPU baseline (rank 0, N = 1) -------------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_sample = 1024
+        dt, cores = oracle_sample(acq, rc, frames, idx, n_sample)
+        cpu = {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_sample} frames of the workload (coefficients, accumulation over all "
+                         f"{S} scan frequencies, deconvolution, inverse DFT); plan build excluded"}
+
+    if rank == 0:
+        lat_ms = np.array(lat) * 1e3
+        out = {
+            "metric": METRIC, "value": S * world / (ms_opt * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_opt, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if path == "fp32" else "f16-split/f32",
+            "data": "synthetic",
+            "config": {"workload": "128x128 scan, 128x128 f32 detector (Poisson 1e4 e-/frame), "
+                                   "Hermite-Gauss K=64, 64-frame pushes, snapshot per step",
+                       "name": WORKLOAD, "path": path, "accum_depth": 1024,
+                       "cuda_graph": True,
+                       "l2": "inputs larger than L2 (1.07 GB of frames per step)"},
+            "baseline_fp32_plain": {"value": S * world / (ms_plain * 1e-3), "unit": UNIT,
+                                    "ms_per_step": ms_plain,
+                                    "speedup": ms_plain / ms_opt,
+                                    "phase_rel_l2_vs_plain": err},
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                           "p99": float(np.percentile(lat_ms, 99)),
+                           "snapshot_every": LATENCY_SNAPSHOT_EVERY},
+            "stage_ms_per_step": stage_ms,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": S * world / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(S * frames_bytes + 4 * S),
+                    "d2h_bytes_per_step": int(4 * S),
+                    "note": "frames read by the kernels from pinned host memory; phase copied back"},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    plain.close()
+    opt.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

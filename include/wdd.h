@@ -1,0 +1,222 @@
+/*
+ * wdd.h -- C ABI of the GB300 live Wigner Distribution Deconvolution library (libwdd.so).
+ *
+ * The library reconstructs the object transfer function of a 4D-STEM scan while the frames
+ * stream in (live WDD, Sect. 6 of Bangun et al., arXiv 2212.01309):
+ *
+ *   plan    (Algorithm 1)  reduced detector basis P, probe autocorrelation Y_v for every scan
+ *                          frequency v, chi_v = P vec(Y_v), Wiener filter
+ *                          W_v = conj(chi_v) / (|chi_v|^2 + eps_eff), active-frequency mask
+ *                          (Sect. 6.3).  Built once, in FP64 on the GPU.
+ *   push    (Algorithm 2)  per frame: c_s = P vec(I_s) (Sect. 5, operator H), then
+ *                          H[v,k] += exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x)) c_s[k]
+ *                          (Eq. outer_prod: partial sums of F_2D I over the frames at hand).
+ *   snapshot / finalize    o_v = sum_k W_v[k] H[v,k]  (Hadamard product with K_v and sum of all
+ *                          elements, Algorithm 2), o <- o / sqrt(o_0) (Eq. 3), and
+ *                          O = conj(IFFT2(o)) (Algorithm 2, last step), at any time in the scan.
+ *
+ * Every entry point returns a wdd_status; WDD_OK is 0.  On any error nothing is enqueued on the
+ * GPU and the plan's state is unchanged; wdd_last_error() returns a one-line explanation
+ * (thread-local, valid until the next call on the same thread).
+ *
+ * Threading: a plan may be used by one host thread at a time.  Different plans are independent.
+ * Memory: a plan owns all its device buffers; callers own frames and result buffers.
+ */
+#ifndef WDD_H
+#define WDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t) passed as an opaque pointer; NULL = legacy default stream. */
+typedef void* wdd_stream_t;
+
+typedef enum {
+    WDD_OK = 0,
+    WDD_ERR_INVALID_ARG = 1,   /* a pointer is NULL, a size is out of range, a flag is unknown */
+    WDD_ERR_OUT_OF_MEMORY = 2, /* device allocation failed or would exceed hbm_budget_bytes */
+    WDD_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in wdd_last_error) */
+    WDD_ERR_SCAN_INDEX = 4,    /* a scan index is outside [0, scan_y * scan_x) */
+    WDD_ERR_STATE = 5,         /* push after finalize, or use of a destroyed plan */
+    WDD_ERR_TIMEOUT = 6,       /* a bounded wait gave up */
+    WDD_ERR_UNSUPPORTED = 7    /* a valid request this build cannot serve (sizes, basis, dtype) */
+} wdd_status;
+
+/* Reduced detector bases.
+ *  FOURIER_FULL  K = det_y * det_x real cos/sin rows of the detector inverse DFT.  Live WDD with
+ *                this basis equals classical WDD (Eq. 2, Eq. 3) exactly.  det_y, det_x <= 64.
+ *  HG_TENSOR     the operator H of Sect. 5: L x L Hermite-Gauss functions (Eq. 5), K = L * L.
+ *  HG_ENERGY     the first K tensor pairs (n_y, n_x) ordered by oscillator energy n_y + n_x
+ *                (Eq. 10), ties broken by smaller n_y; L is the smallest that holds them.
+ * Hermite-Gauss width: sigma = R_bf / sqrt(2 (L - 1) + 1), R_bf = semiconv / (lambda * dk)
+ * pixels, sampled at x_j = j - det_center; each column has unit discrete L2 norm. */
+typedef enum { WDD_BASIS_FOURIER_FULL = 0, WDD_BASIS_HG_TENSOR = 1, WDD_BASIS_HG_ENERGY = 2 } wdd_basis;
+
+/* Arithmetic of the streaming steps.
+ *  FP32   projection and phase accumulation in FP32 FMA on the SIMT cores.
+ *  SPLIT  tensor-core accumulation: phase factors and coefficients split into hi + lo FP16
+ *         parts, three products (hi*hi + lo*hi + hi*lo) accumulated in FP32.  Staged frames are
+ *         accumulated accum_depth at a time. */
+typedef enum { WDD_PREC_FP32 = 0, WDD_PREC_SPLIT = 1 } wdd_precision;
+
+/* Element type of the frames passed to wdd_push_frames. */
+typedef enum { WDD_FRAME_U16 = 0, WDD_FRAME_F32 = 1, WDD_FRAME_F64 = 2 } wdd_frame_dtype;
+
+typedef struct {
+    int32_t scan_y, scan_x;   /* scan grid S_y x S_x; position s = s_y * scan_x + s_x        */
+    double scan_step_m;       /* scan step Delta in metres (equal on both axes, Sect. 6.3)     */
+    int32_t det_y, det_x;     /* detector pixels N_y x N_x                                     */
+    double det_px_inv_m;      /* detector sampling dk in reciprocal metres per pixel           */
+    double voltage_v;         /* acceleration voltage (sets lambda, relativistic)              */
+    double semiconv_rad;      /* semiconvergence angle theta                                   */
+    double defocus_m;         /* probe defocus df: p(k) = A(k) exp(-i pi lambda df |k|^2)      */
+    double epsilon;           /* Wiener epsilon (relative unless eps_absolute)                 */
+    int32_t rank_k;           /* reduced rank K                                                */
+    int32_t basis;            /* wdd_basis                                                     */
+    int32_t precision;        /* wdd_precision                                                 */
+    int32_t frame_dtype;      /* wdd_frame_dtype                                               */
+    int32_t max_batch;        /* most frames per internal launch; larger pushes are split      */
+    int32_t accum_depth;      /* frames staged before the phase accumulation runs; 0 = every
+                                 push is accumulated at once (the plain path)                  */
+    double det_center_y;      /* detector zero-frequency pixel; negative = det_y / 2 (integer) */
+    double det_center_x;
+    int32_t eps_absolute;     /* 1: eps_eff = epsilon; 0: eps_eff = epsilon * max |chi|^2     */
+    int32_t reserved0;
+    int64_t hbm_budget_bytes; /* refuse plans whose device footprint exceeds this; 0 = none   */
+} wdd_params;
+
+/* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
+ * N/2, relative epsilon 1e-3.  Geometry fields are zeroed and must be set by the caller. */
+wdd_status wdd_params_default(wdd_params* p);
+
+typedef struct wdd_plan wdd_plan;
+
+/* Builds a plan (Algorithm 1 and the initialisation of Algorithm 2): bases, Wiener filter and
+ * mask in FP64 on the current CUDA device, then zeroes the accumulator.  Blocks until the plan
+ * is built.  *out receives the plan (owned by the library, freed by wdd_plan_destroy).
+ * Errors: INVALID_ARG (NULL, non-positive sizes, rank not matching the basis, L > 32,
+ * epsilon < 0), UNSUPPORTED (FOURIER_FULL with a detector side > 64, det side > 1024),
+ * OUT_OF_MEMORY, CUDA. */
+wdd_status wdd_plan_create(const wdd_params* p, wdd_plan** out);
+
+/* Releases every device and host buffer of the plan (synchronises with its last stream). */
+wdd_status wdd_plan_destroy(wdd_plan* plan);
+
+/* Streams n frames into the plan (the loop body of Algorithm 2).
+ *  frames    n x det_y x det_x elements of frame_dtype, row-major, zero frequency at
+ *            (det_center_y, det_center_x) (i.e. fftshifted).  Device memory, pinned host memory
+ *            (read by the kernels directly over the host link) or pageable host memory (copied
+ *            through a plan-owned pinned ring).  Borrowed: it must stay valid and unchanged
+ *            until `stream` has passed this push.
+ *  scan_idx  n int32 scan positions s in [0, S), host memory, read before the call returns.
+ *            Duplicate positions accumulate (the method is linear in the frames).
+ *  stream    CUDA stream the work is enqueued on; the plan remembers it for snapshots.
+ * Returns immediately after enqueuing.  Errors: INVALID_ARG, SCAN_INDEX (nothing enqueued,
+ * counters unchanged), STATE (plan finalized), CUDA. */
+wdd_status wdd_push_frames(wdd_plan* plan, const void* frames, const int32_t* scan_idx,
+                           int64_t n, wdd_stream_t stream);
+
+typedef struct {
+    void* obj;                  /* in: device buffer, complex64 [scan_y][scan_x] (re, im)    */
+    float* phase;               /* in: device buffer f32 [scan_y][scan_x] or NULL             */
+    int64_t frames_seen;        /* out: frames pushed so far (host count, exact)              */
+    int64_t positions_covered;  /* out: scan positions with at least one frame                */
+} wdd_result;
+
+/* Reconstructs from every frame pushed so far (Algorithm 2 after any number of iterations):
+ * deconvolution, normalisation by sqrt(o_0) (principal root; skipped while o_0 == 0), conjugated
+ * inverse FFT (numpy ifft2 normalisation 1/S) and phase = atan2(im, re).  Enqueued on the
+ * plan's last stream; out->obj and out->phase are written in stream order.  The plan continues
+ * to accept frames.  Errors: INVALID_ARG (out or out->obj NULL), STATE, CUDA. */
+wdd_status wdd_snapshot(wdd_plan* plan, wdd_result* out);
+
+/* As wdd_snapshot, then marks the plan finished: later pushes return WDD_ERR_STATE.  An
+ * incomplete scan is not an error; positions_covered reports the coverage. */
+wdd_status wdd_finalize(wdd_plan* plan, wdd_result* out);
+
+/* Sets the stream on which the plan's next snapshot, finalize or reset is enqueued (pushes set
+ * it too).  Work already enqueued on the previous stream is ordered before later work on the
+ * new one. */
+wdd_status wdd_set_stream(wdd_plan* plan, wdd_stream_t stream);
+
+/* Zeroes the accumulator, the staged frames and the hit counters so the plan can take a new
+ * acquisition with the same geometry (the Wiener filter is kept).  Enqueued on the plan's last
+ * stream.  Clears the finished state. */
+wdd_status wdd_reset(wdd_plan* plan);
+
+typedef struct {
+    int32_t rank_k;          /* K                                                            */
+    int32_t basis_ly;        /* basis functions along detector rows (L_y)                    */
+    int32_t basis_lx;        /* along detector columns (L_x)                                 */
+    int32_t n_active;        /* active scan frequencies (Sect. 6.3 overlap criterion)        */
+    double eps_eff;          /* epsilon actually added to |chi|^2                            */
+    double wavelength_m;     /* lambda                                                       */
+    double bf_radius_px;     /* bright-field radius R_bf in detector pixels                  */
+    double hg_sigma_px;      /* Hermite-Gauss sigma (0 for the Fourier basis)                */
+    int64_t device_bytes;    /* device memory held by the plan                               */
+    int64_t frames_seen;
+    int64_t positions_covered;
+    int64_t kernel_launches; /* hot-path kernel launches since the plan was created          */
+    int32_t staged;          /* frames projected but not yet accumulated                     */
+    int32_t finished;
+} wdd_plan_info;
+
+/* Reports the plan's derived constants and counters (host-side, no GPU work). */
+wdd_status wdd_plan_get_info(const wdd_plan* plan, wdd_plan_info* out);
+
+/* Hot-path stages, for wdd_get_stage_times. */
+typedef enum {
+    WDD_STAGE_PROJECT = 0,     /* frame ingest + projection (one launch per internal batch)  */
+    WDD_STAGE_ACCUMULATE = 1,  /* phase accumulation (one launch per flush)                   */
+    WDD_STAGE_DECONVOLVE = 2,  /* Wiener deconvolution (one launch per snapshot)              */
+    WDD_STAGE_IDFT = 3,        /* inverse DFT + phase (two launches per snapshot)             */
+    WDD_STAGE_COUNT = 4
+} wdd_stage;
+
+/* Enables (1) or disables (0) CUDA-event timing of every hot-path launch on the plan's stream.
+ * Timing adds two event records per launch; it is off by default. */
+wdd_status wdd_set_stage_timing(wdd_plan* plan, int32_t enable);
+
+/* Synchronises the plan's stream, then reports per stage the summed device time (ms) and the
+ * number of kernel launches timed since the previous call, and clears them.  ms_out and
+ * launches_out each hold WDD_STAGE_COUNT entries (either may be NULL). */
+wdd_status wdd_get_stage_times(wdd_plan* plan, double* ms_out, int64_t* launches_out);
+
+/* Copies the per-position hit counts (uint32 [S], exact host bookkeeping) into host memory. */
+wdd_status wdd_get_hit_counts(const wdd_plan* plan, uint32_t* host_out, int64_t n);
+
+/* Internal arrays that wdd_copy_array can read back (tests and diagnostics). */
+typedef enum {
+    WDD_ARRAY_WEIGHTS = 0,   /* complex64 [S][K]   W_v[k] (zero rows for inactive v)           */
+    WDD_ARRAY_CHI = 1,       /* complex128 [S][M]  chi_v[m] = H(Y_v), M = L_y * L_x (FP64)      */
+    WDD_ARRAY_ACCUM = 2,     /* complex64 [S][K]   H[v][k] accumulated so far (staged frames
+                                                   are flushed first)                         */
+    WDD_ARRAY_COEFF = 3,     /* float32 [n][K]     coefficients c of the most recent push's
+                                                   last internal launch (n = its frame count) */
+    WDD_ARRAY_SPECTRUM = 4,  /* complex64 [S]      o_v of the most recent snapshot            */
+    WDD_ARRAY_BASIS_Y = 5,   /* float64 [N_y][L_y] (complex128 for FOURIER_FULL)               */
+    WDD_ARRAY_BASIS_X = 6,   /* float64 [N_x][L_x] (complex128 for FOURIER_FULL)               */
+    WDD_ARRAY_MASK = 7,      /* uint8 [S]          1 = active frequency                        */
+    WDD_ARRAY_COEFF_INDEX = 8 /* int32 [K][2]      (flat basis index m, 0 = real / 1 = imag)   */
+} wdd_array;
+
+/* Synchronously copies an internal array into host memory.  `bytes` must be at least the
+ * array's size; *written receives the bytes copied.  Errors: INVALID_ARG, CUDA. */
+wdd_status wdd_copy_array(wdd_plan* plan, int32_t which, void* host_dst, int64_t bytes,
+                          int64_t* written);
+
+/* Status name ("WDD_OK", ...) and the calling thread's last error detail. */
+const char* wdd_status_string(wdd_status s);
+const char* wdd_last_error(void);
+
+/* Library version: (major << 16) | minor. */
+int32_t wdd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WDD_H */

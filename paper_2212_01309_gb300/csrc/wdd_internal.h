@@ -1,0 +1,137 @@
+// Internal declarations shared by the translation units of libwdd.so.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wdd.h"
+
+namespace wdd {
+
+// Threads per block used by most kernels.
+constexpr int kThreads = 256;
+// Detector rows handled by one projection CTA.
+constexpr int kProjRows = 16;
+// Frames per projection launch; their scan indices travel as a kernel parameter block.
+constexpr int kLaunchFrames = 256;
+struct IndexBlock {
+    int32_t s[kLaunchFrames];
+};
+// Pinned ring slots for host-side staging of pageable frames.
+constexpr int kRingSlots = 4;
+
+struct RingSlot {
+    void* h_frames = nullptr;      // pinned, allocated on first pageable push
+    cudaEvent_t done = nullptr;    // recorded after the slot's last reader
+    bool used = false;
+};
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace wdd
+
+struct wdd_plan {
+    wdd_params p{};
+    int S = 0, Sy = 0, Sx = 0, Ny = 0, Nx = 0, K = 0, Ly = 0, Lx = 0, M = 0;
+    int complex_basis = 0;   // 1 = Fourier basis (complex 1-D functions)
+    int lcm = 0;             // lcm(Sy, Sx): length of the scan-phase table
+    int depth = 0;           // staging depth (frames accumulated per flush)
+    int max_batch = 0;
+    int chunk = 0;           // frames per projection launch (<= kLaunchFrames)
+    int rb = 0;              // row blocks per frame in the projection
+    double lambda = 0, R = 0, sigma = 0, eps_eff = 0, cy = 0, cx = 0;
+    int n_active = 0;
+
+    // FP64 plan arrays
+    double2* d_By = nullptr;     // [Ny][Ly] complex (imag 0 for Hermite-Gauss)
+    double2* d_Bx = nullptr;     // [Nx][Lx]
+    double* d_qy = nullptr;      // [Sy] probe shift per frequency row, detector pixels
+    double* d_qx = nullptr;      // [Sx]
+    double2* d_chi = nullptr;    // [S][M] (freed after the plan is built unless kept)
+    // FP32 streaming arrays
+    float2* d_By32 = nullptr;    // [Ny][Ly] (complex, imag 0 for Hermite-Gauss)
+    float2* d_Bx32 = nullptr;    // [Nx][Lx]
+    int2* d_ktab = nullptr;      // [K] (flat index m, component)
+    float2* d_W = nullptr;       // [S][K]
+    uint8_t* d_mask = nullptr;   // [S]
+    float2* d_H = nullptr;       // [S][K] accumulator
+    float2* d_tw = nullptr;      // [lcm] exp(-2 pi i m / lcm)
+    uint4* d_tw16 = nullptr;     // [lcm] FP16 hi/lo split of exp(-2 pi i m / lcm)
+    float2* d_twy = nullptr;     // [Sy] exp(+2 pi i m / Sy)  (inverse DFT)
+    float2* d_twx = nullptr;     // [Sx]
+    float* d_cstage = nullptr;   // [depth][K] staged coefficients
+    int32_t* d_idxstage = nullptr;  // [depth]
+    float* d_cpart = nullptr;    // [max_batch][rb][2*M] projection partials
+    unsigned* d_count = nullptr; // [max_batch] projection arrival counters
+    float2* d_o = nullptr;       // [S] spectrum
+    float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
+    __half* d_chalf = nullptr;   // split path: [depth][2][K] FP16 hi/lo coefficients (transposed use)
+
+    // host bookkeeping (exact)
+    std::vector<uint32_t> hits;
+    std::vector<int32_t> h_ktab;
+    int64_t frames_seen = 0;
+    int64_t covered = 0;
+    int staged = 0;
+    int last_coeff_n = 0;
+    int last_coeff_off = 0;
+    bool finished = false;
+    cudaStream_t stream = nullptr;
+    bool stream_set = false;
+    cudaEvent_t handoff = nullptr;  // orders work when the caller switches streams
+    int device = 0;
+
+    wdd::RingSlot ring[wdd::kRingSlots];
+    int ring_next = 0;
+    size_t frame_slot_bytes = 0;
+
+    std::vector<wdd::DevBuf> allocs;
+    int64_t device_bytes = 0;
+
+    // launch accounting and optional per-stage event timing
+    int64_t launches_total = 0;
+    bool timing = false;
+    struct Timed { int stage; int launches; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t untimed_launches[4] = {0, 0, 0, 0};
+};
+
+namespace wdd {
+
+void set_error(const std::string& msg);
+// Raises the dynamic shared-memory limit of every kernel once per process (not per launch, so
+// launches stay legal inside stream capture).
+cudaError_t prepare_kernels();
+cudaError_t prepare_project_kernels();
+cudaError_t prepare_reconstruct_kernels();
+cudaError_t prepare_split_kernels();
+size_t frame_elem_bytes(int dtype);
+
+// ---- plan kernels (FP64) -----------------------------------------------------------------
+cudaError_t launch_hg_basis(double2* B, int n, int L, double sigma, double center, cudaStream_t st);
+cudaError_t launch_fourier_basis(double2* B, int n, double center, cudaStream_t st);
+cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStream_t st);
+cudaError_t launch_weights(const wdd_plan* P, cudaStream_t st);
+cudaError_t launch_tables(const wdd_plan* P, cudaStream_t st);
+
+// ---- streaming kernels ---------------------------------------------------------------------
+cudaError_t launch_project(const wdd_plan* P, const void* frames, int dtype, int n,
+                           const IndexBlock& idx, float* c_out, int32_t* idx_out,
+                           cudaStream_t st);
+cudaError_t launch_accumulate_fp32(const wdd_plan* P, const float* c, const int32_t* idx, int n,
+                                   cudaStream_t st);
+bool split_path_available();
+cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
+                                    cudaStream_t st);
+cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st);
+cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st);
+
+}  // namespace wdd

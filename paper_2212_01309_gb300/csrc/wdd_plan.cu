@@ -1,0 +1,337 @@
+// Plan-time kernels (FP64): reduced bases, projected probe autocorrelation chi_v and the Wiener
+// filter of Algorithm 1, and the scan-phase tables of Algorithm 2's initialisation.
+//
+// Decisions that turn floating point into a yes/no (is a detector point inside the shifted
+// aperture?) are evaluated with explicitly rounded FP64 operations (__dmul_rn / __dadd_rn, no
+// fused multiply-add) in the order ky*ky + kx*kx <= R*R, so that the CPU oracle, which evaluates
+// the same expression in IEEE double, takes the same decision on every pixel.
+
+#include <cuda_fp16.h>
+
+#include "wdd_internal.h"
+
+namespace wdd {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {  // a * conj(b)
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// Normalised 1-D oscillator eigenfunctions (Eq. 5) by the three-term recurrence:
+//   psi_0 = pi^-1/4 exp(-x^2/2), psi_1 = sqrt(2) x psi_0,
+//   psi_{n+1} = sqrt(2/(n+1)) x psi_n - sqrt(n/(n+1)) psi_{n-1},  x = (j - center) / sigma.
+// One thread per sample; column norms are fixed by hg_normalise_kernel.
+__global__ void hg_basis_kernel(double2* B, int n, int L, double sigma, double center) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double x = ((double)j - center) / sigma;
+    double pm1 = 0.0;
+    double p0 = 0.75112554446494248286 * exp(-0.5 * x * x);  // pi^(-1/4)
+    B[(size_t)j * L] = make_double2(p0, 0.0);
+    if (L > 1) {
+        double p1 = 1.41421356237309504880 * x * p0;
+        B[(size_t)j * L + 1] = make_double2(p1, 0.0);
+        pm1 = p0;
+        p0 = p1;
+        for (int k = 1; k < L - 1; ++k) {
+            double nxt = sqrt(2.0 / (k + 1)) * x * p0 - sqrt((double)k / (k + 1.0)) * pm1;
+            B[(size_t)j * L + k + 1] = make_double2(nxt, 0.0);
+            pm1 = p0;
+            p0 = nxt;
+        }
+    }
+}
+
+// Scales every column of B (n x L) to unit discrete L2 norm; one block per column.
+__global__ void hg_normalise_kernel(double2* B, int n, int L) {
+    __shared__ double red[kThreads];
+    int col = blockIdx.x;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = B[(size_t)j * L + col].x;
+        s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double nrm = sqrt(red[0]);
+    if (nrm == 0.0) nrm = 1.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) B[(size_t)j * L + col].x /= nrm;
+}
+
+// Fourier family: B[j][r] = exp(+2 pi i (j - center) r / n) / n (inverse-DFT rows).
+__global__ void fourier_basis_kernel(double2* B, int n, double center) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n) return;
+    int j = t / n, r = t % n;
+    double s, c;
+    sincospi(2.0 * (((double)j - center) * (double)r) / (double)n, &s, &c);
+    B[t] = make_double2(c / n, s / n);
+}
+
+constexpr int kChiRows = 8;
+
+// Probe spectrum at a detector point k (pixels) given its squared radius k2 (already rounded):
+// A(k) exp(-i coef k2) with A the hard-edged aperture |k|^2 <= R^2.
+__device__ __forceinline__ double2 probe_at(double k2, double R2, double coef) {
+    if (!(k2 <= R2)) return make_double2(0.0, 0.0);
+    if (coef == 0.0) return make_double2(1.0, 0.0);
+    double s, c;
+    sincos(__dmul_rn(coef, k2), &s, &c);
+    return make_double2(c, -s);
+}
+
+// chi_v = By^T Y_v Bx for one scan frequency v per block, Y_v(q) = p(q) conj p(q + q_v)
+// (Algorithm 1).  Y is built row block by row block in shared memory; Z accumulates in registers.
+// Also folds max |chi_v[m]|^2 over the used indices into *maxbits (as ordered uint64 bits).
+template <int ZPT>
+__global__ void __launch_bounds__(kThreads)
+chi_kernel(const double2* __restrict__ By, const double2* __restrict__ Bx,
+           const double* __restrict__ qy, const double* __restrict__ qx,
+           const uint8_t* __restrict__ used, double2* __restrict__ chi,
+           unsigned long long* maxbits, int Sx, int Ny, int Nx, int Ly, int Lx,
+           double cy, double cx, double R, double R2, double coef) {
+    extern __shared__ double2 sm[];
+    double2* sBx = sm;                          // Nx * Lx
+    double2* sY = sBx + (size_t)Nx * Lx;        // kChiRows * Nx
+    double2* sT = sY + (size_t)kChiRows * Nx;   // kChiRows * Lx
+    __shared__ double red[kThreads];
+
+    const int v = blockIdx.x;
+    const double shy = qy[v / Sx];
+    const double shx = qx[v % Sx];
+    const int M = Ly * Lx;
+
+    for (int t = threadIdx.x; t < Nx * Lx; t += blockDim.x) sBx[t] = Bx[t];
+
+    double2 z[ZPT];
+#pragma unroll
+    for (int u = 0; u < ZPT; ++u) z[u] = make_double2(0.0, 0.0);
+
+    for (int i0 = 0; i0 < Ny; i0 += kChiRows) {
+        // skip row blocks that lie entirely outside the unshifted aperture
+        double dlo = (double)i0 - cy, dhi = (double)(i0 + kChiRows - 1) - cy;
+        double dmin = (dlo > 0) ? dlo : ((dhi < 0) ? -dhi : 0.0);
+        if (dmin > R + 1.0) continue;
+        __syncthreads();
+        for (int t = threadIdx.x; t < kChiRows * Nx; t += blockDim.x) {
+            int r = t / Nx, j = t % Nx, i = i0 + r;
+            double2 y = make_double2(0.0, 0.0);
+            if (i < Ny) {
+                double ky = (double)i - cy;
+                double kx = (double)j - cx;
+                double k2 = __dadd_rn(__dmul_rn(ky, ky), __dmul_rn(kx, kx));
+                double2 a = probe_at(k2, R2, coef);
+                if (a.x != 0.0 || a.y != 0.0) {
+                    double ky2 = __dadd_rn(ky, shy);
+                    double kx2 = __dadd_rn(kx, shx);
+                    double k2s = __dadd_rn(__dmul_rn(ky2, ky2), __dmul_rn(kx2, kx2));
+                    double2 b = probe_at(k2s, R2, coef);
+                    y = cmul_conj(a, b);
+                }
+            }
+            sY[t] = y;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kChiRows * Lx; t += blockDim.x) {
+            int r = t / Lx, lx = t % Lx;
+            double2 acc = make_double2(0.0, 0.0);
+            const double2* yr = sY + (size_t)r * Nx;
+            for (int j = 0; j < Nx; ++j) {
+                double2 y = yr[j];
+                double2 b = sBx[(size_t)j * Lx + lx];
+                acc.x += y.x * b.x - y.y * b.y;
+                acc.y += y.x * b.y + y.y * b.x;
+            }
+            sT[t] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < ZPT; ++u) {
+            int o = threadIdx.x + u * kThreads;
+            if (o < M) {
+                int ly = o / Lx, lx = o % Lx;
+                for (int r = 0; r < kChiRows && i0 + r < Ny; ++r) {
+                    double2 b = By[(size_t)(i0 + r) * Ly + ly];
+                    double2 tt = sT[r * Lx + lx];
+                    z[u].x += b.x * tt.x - b.y * tt.y;
+                    z[u].y += b.x * tt.y + b.y * tt.x;
+                }
+            }
+        }
+    }
+    double mx = 0.0;
+#pragma unroll
+    for (int u = 0; u < ZPT; ++u) {
+        int o = threadIdx.x + u * kThreads;
+        if (o < M) {
+            chi[(size_t)v * M + o] = z[u];
+            if (used[o]) {
+                double a2 = z[u].x * z[u].x + z[u].y * z[u].y;
+                mx = a2 > mx ? a2 : mx;
+            }
+        }
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+__device__ __forceinline__ double2 wiener(double2 z, double eps) {
+    double d = z.x * z.x + z.y * z.y + eps;
+    return make_double2(z.x / d, -z.y / d);
+}
+
+// W_v[k] from chi_v (Algorithm 1: K_v = conj(chi_v) / (|chi_v|^2 + eps_eff)).  Hermite-Gauss
+// rows take K_v[m_k]; Fourier cos/sin rows pair r with -r:
+//   W[cos r] = K(r) + K(-r)  (K(r) when r = -r),  W[sin r] = i (K(r) - K(-r)).
+__global__ void weights_kernel(const double2* __restrict__ chi, const int2* __restrict__ ktab,
+                               const uint8_t* __restrict__ mask, float2* __restrict__ W,
+                               int S, int K, int Ly, int Lx, int complex_basis, double eps) {
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)S * K) return;
+    int v = (int)(t / K), k = (int)(t % K);
+    if (!mask[v]) {
+        W[t] = make_float2(0.f, 0.f);
+        return;
+    }
+    int M = Ly * Lx;
+    int2 e = ktab[k];
+    double2 Kr = wiener(chi[(size_t)v * M + e.x], eps);
+    double2 w;
+    if (!complex_basis) {
+        w = Kr;
+    } else {
+        int ry = e.x / Lx, rx = e.x % Lx;
+        int mn = ((Ly - ry) % Ly) * Lx + (Lx - rx) % Lx;
+        double2 Kn = wiener(chi[(size_t)v * M + mn], eps);
+        if (e.y == 0) {
+            w = (mn == e.x) ? Kr : make_double2(Kr.x + Kn.x, Kr.y + Kn.y);
+        } else {
+            // i * (Kr - Kn)
+            w = make_double2(-(Kr.y - Kn.y), Kr.x - Kn.x);
+        }
+    }
+    W[t] = make_float2((float)w.x, (float)w.y);
+}
+
+// exp(-2 pi i m / lcm) (forward scan phase) in FP32 and as an FP16 hi/lo split, and the inverse
+// DFT twiddles exp(+2 pi i m / n) for both scan axes.
+__global__ void tables_kernel(float2* tw, uint4* tw16, int lcm, float2* twy, int Sy, float2* twx,
+                              int Sx) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < lcm) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)lcm, &s, &c);
+        double re = c, im = -s;
+        tw[t] = make_float2((float)re, (float)im);
+        __half rh = __double2half(re);
+        __half rl = __double2half(re - (double)__half2float(rh));
+        __half ih = __double2half(im);
+        __half il = __double2half(im - (double)__half2float(ih));
+        uint4 q;
+        q.x = __half_as_ushort(rh);
+        q.y = __half_as_ushort(rl);
+        q.z = __half_as_ushort(ih);
+        q.w = __half_as_ushort(il);
+        tw16[t] = q;
+    }
+    if (t < Sy) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)Sy, &s, &c);
+        twy[t] = make_float2((float)c, (float)s);
+    }
+    if (t < Sx) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)Sx, &s, &c);
+        twx[t] = make_float2((float)c, (float)s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_hg_basis(double2* B, int n, int L, double sigma, double center, cudaStream_t st) {
+    hg_basis_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, n, L, sigma, center);
+    hg_normalise_kernel<<<L, kThreads, 0, st>>>(B, n, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_basis(double2* B, int n, double center, cudaStream_t st) {
+    fourier_basis_kernel<<<(n * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, n, center);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStream_t st) {
+    // used-index flags
+    std::vector<uint8_t> used(P->M, 0);
+    for (int k = 0; k < P->K; ++k) {
+        int m = P->h_ktab[2 * k];
+        used[m] = 1;
+        if (P->complex_basis) {
+            int ry = m / P->Lx, rx = m % P->Lx;
+            used[((P->Ly - ry) % P->Ly) * P->Lx + (P->Lx - rx) % P->Lx] = 1;
+        }
+    }
+    uint8_t* d_used = nullptr;
+    cudaError_t e = cudaMalloc(&d_used, P->M);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_used, used.data(), P->M, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cudaFree(d_used); return e; }
+    size_t smem = sizeof(double2) * ((size_t)P->Nx * P->Lx + (size_t)kChiRows * P->Nx +
+                                     (size_t)kChiRows * P->Lx);
+    int zpt = (P->M + kThreads - 1) / kThreads;
+    double R2 = P->R * P->R;
+    double coef = 3.14159265358979323846 * P->lambda * P->p.defocus_m *
+                  (P->p.det_px_inv_m * P->p.det_px_inv_m);
+#define WDD_CHI(Z)                                                                                \
+    do {                                                                                          \
+        e = cudaFuncSetAttribute(chi_kernel<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 (int)smem);                                                      \
+        if (e == cudaSuccess)                                                                     \
+            chi_kernel<Z><<<P->S, kThreads, smem, st>>>(P->d_By, P->d_Bx, P->d_qy, P->d_qx,       \
+                                                        d_used, P->d_chi, d_maxbits, P->Sx,       \
+                                                        P->Ny, P->Nx, P->Ly, P->Lx, P->cy, P->cx, \
+                                                        P->R, R2, coef);                          \
+    } while (0)
+    if (zpt <= 1) WDD_CHI(1);
+    else if (zpt <= 2) WDD_CHI(2);
+    else if (zpt <= 4) WDD_CHI(4);
+    else if (zpt <= 8) WDD_CHI(8);
+    else if (zpt <= 16) WDD_CHI(16);
+    else e = cudaErrorInvalidValue;
+#undef WDD_CHI
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(d_used);
+    return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t launch_weights(const wdd_plan* P, cudaStream_t st) {
+    size_t n = (size_t)P->S * P->K;
+    weights_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        P->d_chi, P->d_ktab, P->d_mask, P->d_W, P->S, P->K, P->Ly, P->Lx, P->complex_basis,
+        P->eps_eff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const wdd_plan* P, cudaStream_t st) {
+    int n = P->lcm;
+    if (P->Sy > n) n = P->Sy;
+    if (P->Sx > n) n = P->Sx;
+    tables_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+        P->d_tw, P->d_tw16, P->lcm, P->d_twy, P->Sy, P->d_twx, P->Sx);
+    return cudaGetLastError();
+}
+
+}  // namespace wdd

@@ -1,0 +1,141 @@
+// Snapshot reconstruction (Algorithm 2, after the frame loop; Eq. 3):
+//   o_v = sum_k W_v[k] H[v, k]                 (Hadamard product with K_v, sum of all elements)
+//   O   = conj( IDFT2( o / sqrt(o_0) ) )        (numpy ifft2 normalisation 1/S)
+//   phase = atan2(Im O, Re O)
+// The deconvolution reads H and W once (HBM bound) and accumulates in FP64; the inverse DFT runs
+// row-column on the S_y x S_x spectrum with exact integer twiddle indices.
+
+#include "wdd_internal.h"
+
+namespace wdd {
+
+namespace {
+
+// one warp per scan frequency
+__global__ void deconvolve_kernel(const float2* __restrict__ W, const float2* __restrict__ H,
+                                  float2* __restrict__ o, int S, int K) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= S) return;
+    const float2* w = W + (size_t)warp * K;
+    const float2* h = H + (size_t)warp * K;
+    double re = 0.0, im = 0.0;
+    for (int k = lane; k < K; k += 32) {
+        float2 a = __ldg(w + k);
+        float2 b = __ldcg(h + k);
+        re += (double)a.x * b.x - (double)a.y * b.y;
+        im += (double)a.x * b.y + (double)a.y * b.x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, off);
+        im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) o[warp] = make_float2((float)re, (float)im);
+}
+
+// 1 / sqrt(z) with the principal square root; 1 when z == 0.  The root is formed without
+// cancellation: t = sqrt((|z| + |x|) / 2) gives the larger component and y / (2 t) the other,
+// so a rounded |z| slightly below |x| cannot produce the square root of a negative number.
+__device__ double2 inv_principal_sqrt(float2 zf) {
+    double x = zf.x, y = zf.y;
+    if (x == 0.0 && y == 0.0) return make_double2(1.0, 0.0);
+    double r = hypot(x, y);
+    double t = sqrt(0.5 * (r + fabs(x)));
+    double sr, si;
+    if (x >= 0.0) {
+        sr = t;
+        si = y / (2.0 * t);
+    } else {
+        sr = fabs(y) / (2.0 * t);
+        si = copysign(t, y);
+    }
+    double d = sr * sr + si * si;
+    return make_double2(sr / d, -si / d);
+}
+
+// pass 1: X[vy][x] = sum_vx (o[vy][vx] / sqrt(o_0)) exp(+2 pi i vx x / Sx); one CTA per row
+__global__ void idft_rows_kernel(const float2* __restrict__ o, const float2* __restrict__ twx,
+                                 float2* __restrict__ X, int Sy, int Sx) {
+    extern __shared__ float2 sm2[];
+    float2* srow = sm2;        // Sx
+    float2* stw = sm2 + Sx;    // Sx
+    const int vy = blockIdx.x;
+    double2 sc = inv_principal_sqrt(o[0]);
+    float scr = (float)sc.x, sci = (float)sc.y;
+    for (int t = threadIdx.x; t < Sx; t += blockDim.x) {
+        float2 a = o[(size_t)vy * Sx + t];
+        srow[t] = make_float2(a.x * scr - a.y * sci, a.x * sci + a.y * scr);
+        stw[t] = twx[t];
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < Sx; x += blockDim.x) {
+        float re = 0.f, im = 0.f;
+        int m = 0;
+        for (int vx = 0; vx < Sx; ++vx) {
+            float2 a = srow[vx], w = stw[m];
+            re = fmaf(a.x, w.x, fmaf(-a.y, w.y, re));
+            im = fmaf(a.x, w.y, fmaf(a.y, w.x, im));
+            m += x;
+            if (m >= Sx) m -= Sx;
+        }
+        X[(size_t)vy * Sx + x] = make_float2(re, im);
+    }
+}
+
+// pass 2: O[y][x] = conj( sum_vy X[vy][x] exp(+2 pi i vy y / Sy) ) / S; one CTA per column
+__global__ void idft_cols_kernel(const float2* __restrict__ X, const float2* __restrict__ twy,
+                                 float2* __restrict__ obj, float* __restrict__ phase, int Sy,
+                                 int Sx) {
+    extern __shared__ float2 sm2[];
+    float2* scol = sm2;        // Sy
+    float2* stw = sm2 + Sy;    // Sy
+    const int x = blockIdx.x;
+    for (int t = threadIdx.x; t < Sy; t += blockDim.x) {
+        scol[t] = X[(size_t)t * Sx + x];
+        stw[t] = twy[t];
+    }
+    __syncthreads();
+    const float inv = 1.0f / (float)((double)Sy * (double)Sx);
+    for (int y = threadIdx.x; y < Sy; y += blockDim.x) {
+        float re = 0.f, im = 0.f;
+        int m = 0;
+        for (int vy = 0; vy < Sy; ++vy) {
+            float2 a = scol[vy], w = stw[m];
+            re = fmaf(a.x, w.x, fmaf(-a.y, w.y, re));
+            im = fmaf(a.x, w.y, fmaf(a.y, w.x, im));
+            m += y;
+            if (m >= Sy) m -= Sy;
+        }
+        float2 r = make_float2(re * inv, -im * inv);
+        obj[(size_t)y * Sx + x] = r;
+        if (phase) phase[(size_t)y * Sx + x] = atan2f(r.y, r.x);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st) {
+    int warps_per_block = kThreads / 32;
+    int blocks = (P->S + warps_per_block - 1) / warps_per_block;
+    deconvolve_kernel<<<blocks, kThreads, 0, st>>>(P->d_W, P->d_H, P->d_o, P->S, P->K);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_reconstruct_kernels() {
+    const int lim = 227 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(idft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(idft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return e;
+}
+
+cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st) {
+    idft_rows_kernel<<<P->Sy, kThreads, 2 * sizeof(float2) * P->Sx, st>>>(P->d_o, P->d_twx,
+                                                                         P->d_tmp, P->Sy, P->Sx);
+    idft_cols_kernel<<<P->Sx, kThreads, 2 * sizeof(float2) * P->Sy, st>>>(P->d_tmp, P->d_twy, obj,
+                                                                         phase, P->Sy, P->Sx);
+    return cudaGetLastError();
+}
+
+}  // namespace wdd

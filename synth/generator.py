@@ -26,6 +26,15 @@ from typing import Iterator
 
 import numpy as np
 
+try:  # multi-threaded FFTs when scipy is present (same transform as numpy's)
+    import scipy.fft as _sfft
+
+    def _fft2(a):
+        return _sfft.fft2(a, axes=(-2, -1), workers=-1)
+except ImportError:  # pragma: no cover
+    def _fft2(a):
+        return np.fft.fft2(a, axes=(-2, -1))
+
 # CODATA 2018 constants (SI).
 _H = 6.62607015e-34
 _M0 = 9.1093837015e-31
@@ -204,8 +213,8 @@ def _frames_clean(acq: Acquisition, obj: np.ndarray, probe: np.ndarray,
     rows = (oy[:, None] + ar[None, :]) % acq.obj_y
     cols = (ox[:, None] + ar[None, :]) % acq.obj_x
     patch = obj[rows[:, :, None], cols[:, None, :]]
-    wave = np.fft.fft2(patch * probe[None, :, :], axes=(-2, -1))
-    inten = np.abs(wave) ** 2
+    wave = _fft2(patch * probe[None, :, :])
+    inten = wave.real * wave.real + wave.imag * wave.imag
     return np.fft.fftshift(inten, axes=(-2, -1))
 
 

@@ -1,0 +1,93 @@
+"""The C ABI: libwdd.so loads, exports every entry point include/wdd.h declares, the binding's
+struct layouts match the C compiler's, and host-side validation errors need no GPU."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wdd.h")
+
+
+@pytest.fixture(scope="module")
+def wdd():
+    from paper_2212_01309_gb300 import build, wdd
+    if not os.path.exists(wdd.LIB_PATH):
+        build.build()
+    wdd.lib()
+    return wdd
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wdd_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for required in ("wdd_plan_create", "wdd_push_frames", "wdd_snapshot", "wdd_finalize",
+                     "wdd_plan_destroy", "wdd_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(wdd):
+    L = wdd.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert set(wdd.exported_symbols()) >= set(declared_functions())
+
+
+def test_status_strings(wdd):
+    L = wdd.lib()
+    assert L.wdd_status_string(0) == b"WDD_OK"
+    assert L.wdd_status_string(4) == b"WDD_ERR_SCAN_INDEX"
+    assert L.wdd_version() >> 16 == 0
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_struct_layout_matches_c(wdd, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "wdd.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(wdd_params),"
+        " offsetof(wdd_params, rank_k), offsetof(wdd_params, det_center_y),"
+        " offsetof(wdd_params, hbm_budget_bytes), sizeof(wdd_result), sizeof(wdd_plan_info));"
+        "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                       check=True).stdout.split()))
+    P = wdd.Params
+    assert got == [ctypes.sizeof(P), P.rank_k.offset, P.det_center_y.offset,
+                   P.hbm_budget_bytes.offset, ctypes.sizeof(wdd.Result),
+                   ctypes.sizeof(wdd.PlanInfo)]
+
+
+def test_invalid_params_rejected_on_host(wdd):
+    L = wdd.lib()
+    p = wdd.Params()
+    assert L.wdd_params_default(ctypes.byref(p)) == 0
+    h = ctypes.c_void_p()
+    # zero geometry
+    assert L.wdd_plan_create(ctypes.byref(p), ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+    assert b"positive" in L.wdd_last_error()
+    p2 = wdd.make_params(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=16, det_x=16,
+                         det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=15)
+    assert L.wdd_plan_create(ctypes.byref(p2), ctypes.byref(h)) == wdd.ERR_INVALID_ARG  # not square
+    p3 = wdd.make_params(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=128, det_x=128,
+                         det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02,
+                         rank_k=128 * 128, basis="fourier_full")
+    assert L.wdd_plan_create(ctypes.byref(p3), ctypes.byref(h)) == wdd.ERR_UNSUPPORTED
+    p4 = wdd.make_params(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=16, det_x=16,
+                         det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=16,
+                         epsilon=-1.0)
+    assert L.wdd_plan_create(ctypes.byref(p4), ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+    assert L.wdd_plan_create(None, ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+    assert L.wdd_push_frames(None, None, None, 0, None) == wdd.ERR_INVALID_ARG
+    assert L.wdd_snapshot(None, None) == wdd.ERR_INVALID_ARG
+    assert L.wdd_plan_destroy(None) == wdd.ERR_INVALID_ARG
