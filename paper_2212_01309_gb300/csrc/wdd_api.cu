@@ -50,6 +50,18 @@ int signed_freq(int v, int n) { return (v <= (n - 1) / 2) ? v : v - n; }
 
 }  // namespace
 
+cudaError_t allow_max_dynamic_smem(const void* func) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 cudaError_t prepare_kernels() {
     static cudaError_t status = [] {
         cudaError_t e = prepare_project_kernels();

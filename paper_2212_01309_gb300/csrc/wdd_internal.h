@@ -110,6 +110,8 @@ void set_error(const std::string& msg);
 // Raises the dynamic shared-memory limit of every kernel once per process (not per launch, so
 // launches stay legal inside stream capture).
 cudaError_t prepare_kernels();
+// Sets a kernel's dynamic shared-memory limit to the device opt-in maximum minus its static use.
+cudaError_t allow_max_dynamic_smem(const void* func);
 cudaError_t prepare_project_kernels();
 cudaError_t prepare_reconstruct_kernels();
 cudaError_t prepare_split_kernels();

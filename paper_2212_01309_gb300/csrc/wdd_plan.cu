@@ -296,8 +296,7 @@ cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStr
                   (P->p.det_px_inv_m * P->p.det_px_inv_m);
 #define WDD_CHI(Z)                                                                                \
     do {                                                                                          \
-        e = cudaFuncSetAttribute(chi_kernel<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                 (int)smem);                                                      \
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(chi_kernel<Z>));                 \
         if (e == cudaSuccess)                                                                     \
             chi_kernel<Z><<<P->S, kThreads, smem, st>>>(P->d_By, P->d_Bx, P->d_qy, P->d_qx,       \
                                                         d_used, P->d_chi, d_maxbits, P->Sx,       \

@@ -151,12 +151,9 @@ cudaError_t launch_typed(const wdd_plan* P, const FT* frames, int n, const Index
 
 template <typename FT>
 cudaError_t prepare_typed() {
-    const int lim = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(project_kernel<FT, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(project_kernel<FT, true>));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(project_kernel<FT, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(project_kernel<FT, false>));
     return e;
 }
 

@@ -123,10 +123,8 @@ cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st) {
 }
 
 cudaError_t prepare_reconstruct_kernels() {
-    const int lim = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(idft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(idft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(idft_rows_kernel));
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(reinterpret_cast<const void*>(idft_cols_kernel));
     return e;
 }
 
