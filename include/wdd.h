@@ -185,6 +185,17 @@ wdd_status wdd_set_stage_timing(wdd_plan* plan, int32_t enable);
  * launches_out each hold WDD_STAGE_COUNT entries (either may be NULL). */
 wdd_status wdd_get_stage_times(wdd_plan* plan, double* ms_out, int64_t* launches_out);
 
+/* Synchronises the plan's stream and reports whether any of its kernels gave up a bounded
+ * device wait (tensor-core pipeline barriers wait at most ~2 s).  Returns WDD_ERR_TIMEOUT and
+ * clears the flag if one did; the CUDA context stays usable and the accumulator must be
+ * considered invalid (wdd_reset). */
+wdd_status wdd_check_device(wdd_plan* plan);
+
+/* Runs the library's bounded device wait on a barrier that nothing completes, with a limit of
+ * wait_ns nanoseconds (1 .. 1e10).  Returns WDD_ERR_TIMEOUT when the wait gave up as designed
+ * (the expected result), WDD_OK if it did not, WDD_ERR_CUDA on a CUDA error. */
+wdd_status wdd_selftest_bounded_wait(int64_t wait_ns);
+
 /* Copies the per-position hit counts (uint32 [S], exact host bookkeeping) into host memory. */
 wdd_status wdd_get_hit_counts(const wdd_plan* plan, uint32_t* host_out, int64_t n);
 

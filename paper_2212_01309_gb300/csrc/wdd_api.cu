@@ -139,11 +139,11 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += 8LL * P->K;                                        // coefficient table
     b += 8LL * P->S * P->K * 2;                             // W and H
     b += (int64_t)P->S;                                     // mask
-    b += 24LL * P->lcm + 8LL * (P->Sy + P->Sx);             // tables
+    b += 16LL * P->lcm + 8LL * (P->Sy + P->Sx);             // tables
     b += 4LL * P->depth * P->K + 4LL * P->depth;            // staging
     b += 4LL * P->chunk * P->rb * P->K + 4LL * P->chunk;     // projection partials
     b += 16LL * P->S;                                       // spectrum + DFT scratch
-    b += 8LL * P->depth * P->K;                             // FP16 split coefficients
+    b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
     return b;
 }
 
@@ -303,6 +303,11 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     P->max_batch = p.max_batch;
     P->chunk = std::min(p.max_batch, kLaunchFrames);
     P->depth = p.accum_depth > 0 ? std::max(p.accum_depth, p.max_batch) : p.max_batch;
+    P->depth_pad = (P->depth + 31) / 32 * 32;
+    if (p.precision == WDD_PREC_SPLIT && P->depth_pad > 8192) {
+        delete P;
+        return fail(WDD_ERR_INVALID_ARG, "split precision stages at most 8192 frames");
+    }
     P->lcm = std::lcm(P->Sy, P->Sx);
     P->rb = (P->Ny + kProjRows - 1) / kProjRows;
     cudaGetDevice(&P->device);
@@ -372,7 +377,8 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
         int cw = P->complex_basis ? 2 : 1;
         size_t proj = 4u * ((size_t)P->Nx * P->Lx * cw + (size_t)kProjRows * P->Nx +
                             (size_t)kProjRows * P->Lx * cw);
-        if (chi > lim || proj > lim) {
+        size_t tc = p.precision == WDD_PREC_SPLIT ? split_smem_bytes(split_tile_n(P->K)) : 0;
+        if (chi > lim || proj > lim || tc > lim) {
             delete P;
             return fail(WDD_ERR_UNSUPPORTED, "detector width times basis order too large");
         }
@@ -443,13 +449,20 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     WDD_ALLOC(P->d_tw16, P->lcm);
     WDD_ALLOC(P->d_twy, P->Sy);
     WDD_ALLOC(P->d_twx, P->Sx);
-    WDD_ALLOC(P->d_cstage, (size_t)P->depth * P->K);
-    WDD_ALLOC(P->d_idxstage, P->depth);
+    WDD_ALLOC(P->d_cstage, (size_t)P->depth_pad * P->K);
+    WDD_ALLOC(P->d_idxstage, P->depth_pad);
+    WDD_ALLOC(P->d_status, 1);
     WDD_ALLOC(P->d_cpart, (size_t)P->chunk * P->rb * P->K);
     WDD_ALLOC(P->d_count, P->chunk);
     WDD_ALLOC(P->d_o, P->S);
     WDD_ALLOC(P->d_tmp, P->S);
-    if (p.precision == WDD_PREC_SPLIT) WDD_ALLOC(P->d_chalf, (size_t)P->depth * 2 * P->K);
+    if (p.precision == WDD_PREC_SPLIT) {
+        int NT = split_tile_n(P->K);
+        int Kp = (P->K + NT - 1) / NT * NT;
+        WDD_ALLOC(P->d_bsplit, (size_t)2 * Kp * P->depth_pad);
+        WDD_ALLOC(P->d_scale_inv, Kp);
+        WDD_ALLOC(P->d_colmax, P->K);
+    }
 #undef WDD_ALLOC
 
     cudaStream_t s0 = nullptr;
@@ -497,6 +510,10 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     if ((e = launch_tables(P, s0))) return cbail(e, "phase tables");
     if ((e = cudaMemset(P->d_H, 0, 8 * (size_t)P->S * P->K))) return cbail(e, "zero accumulator");
     if ((e = cudaMemset(P->d_count, 0, 4 * (size_t)P->chunk))) return cbail(e, "zero counters");
+    if ((e = cudaMemset(P->d_idxstage, 0, 4 * (size_t)P->depth_pad))) return cbail(e, "zero staging");
+    if ((e = cudaMemset(P->d_cstage, 0, 4 * (size_t)P->depth_pad * P->K))) return cbail(e, "zero staging");
+    if ((e = cudaMemset(P->d_status, 0, 4))) return cbail(e, "zero status");
+    if (P->d_colmax && (e = cudaMemset(P->d_colmax, 0, 4 * (size_t)P->K))) return cbail(e, "zero column max");
     if ((e = cudaDeviceSynchronize())) return cbail(e, "plan build");
 
     // keep chi for inspection only when it is small
@@ -641,6 +658,7 @@ wdd_status wdd_set_stream(wdd_plan* P, wdd_stream_t stream) {
 wdd_status wdd_reset(wdd_plan* P) {
     if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
     WDD_CUDA(cudaMemsetAsync(P->d_H, 0, 8 * (size_t)P->S * P->K, P->stream));
+    if (P->d_colmax) WDD_CUDA(cudaMemsetAsync(P->d_colmax, 0, 4 * (size_t)P->K, P->stream));
     P->staged = 0;
     P->frames_seen = 0;
     P->covered = 0;
@@ -692,6 +710,34 @@ wdd_status wdd_get_stage_times(wdd_plan* P, double* ms_out, int64_t* launches_ou
         if (ms_out) ms_out[s] = ms[s];
         if (launches_out) launches_out[s] = cnt[s];
     }
+    return WDD_OK;
+}
+
+wdd_status wdd_check_device(wdd_plan* P) {
+    if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
+    WDD_CUDA(cudaStreamSynchronize(P->stream));
+    unsigned code = 0;
+    WDD_CUDA(cudaMemcpy(&code, P->d_status, 4, cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        WDD_CUDA(cudaMemset(P->d_status, 0, 4));
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "a device wait gave up (code %u)", code);
+        return fail(WDD_ERR_TIMEOUT, buf);
+    }
+    return WDD_OK;
+}
+
+wdd_status wdd_selftest_bounded_wait(int64_t wait_ns) {
+    if (wait_ns <= 0 || wait_ns > 10000000000LL) return fail(WDD_ERR_INVALID_ARG, "wait_ns out of range");
+    unsigned* d = nullptr;
+    WDD_CUDA(cudaMalloc(&d, 4));
+    cudaError_t e = cudaMemset(d, 0, 4);
+    if (e == cudaSuccess) e = launch_bounded_wait_selftest(d, (uint64_t)wait_ns, nullptr);
+    unsigned code = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&code, d, 4, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self test");
+    if (code == 7u) return fail(WDD_ERR_TIMEOUT, "the device wait gave up as designed");
     return WDD_OK;
 }
 

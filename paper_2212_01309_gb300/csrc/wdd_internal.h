@@ -63,7 +63,7 @@ struct wdd_plan {
     uint8_t* d_mask = nullptr;   // [S]
     float2* d_H = nullptr;       // [S][K] accumulator
     float2* d_tw = nullptr;      // [lcm] exp(-2 pi i m / lcm)
-    uint4* d_tw16 = nullptr;     // [lcm] FP16 hi/lo split of exp(-2 pi i m / lcm)
+    uint2* d_tw16 = nullptr;     // [lcm] FP16 hi/lo split of exp(-2 pi i m / lcm), packed
     float2* d_twy = nullptr;     // [Sy] exp(+2 pi i m / Sy)  (inverse DFT)
     float2* d_twx = nullptr;     // [Sx]
     float* d_cstage = nullptr;   // [depth][K] staged coefficients
@@ -72,7 +72,11 @@ struct wdd_plan {
     unsigned* d_count = nullptr; // [max_batch] projection arrival counters
     float2* d_o = nullptr;       // [S] spectrum
     float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
-    __half* d_chalf = nullptr;   // split path: [depth][2][K] FP16 hi/lo coefficients (transposed use)
+    uint16_t* d_bsplit = nullptr;  // split path: FP16 hi/lo coefficients in the UMMA B layout
+    float* d_scale_inv = nullptr;  // split path: [Kp] inverse power-of-two column scales
+    unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
+    unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
+    int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
 
     // host bookkeeping (exact)
     std::vector<uint32_t> hits;
@@ -127,10 +131,15 @@ cudaError_t launch_tables(const wdd_plan* P, cudaStream_t st);
 // ---- streaming kernels ---------------------------------------------------------------------
 cudaError_t launch_project(const wdd_plan* P, const void* frames, int dtype, int n,
                            const IndexBlock& idx, float* c_out, int32_t* idx_out,
-                           cudaStream_t st);
+                           cudaStream_t st);  // also folds |c| into d_colmax when it is set
 cudaError_t launch_accumulate_fp32(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                    cudaStream_t st);
+// Device-side waits give up after this long and report WDD_ERR_TIMEOUT.
+constexpr uint64_t kDeviceWaitNs = 2000000000ull;
 bool split_path_available();
+int split_tile_n(int K);
+size_t split_smem_bytes(int NT);
+cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cudaStream_t st);
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st);
 cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st);

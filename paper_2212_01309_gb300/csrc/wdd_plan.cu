@@ -226,9 +226,10 @@ __global__ void weights_kernel(const double2* __restrict__ chi, const int2* __re
     W[t] = make_float2((float)w.x, (float)w.y);
 }
 
-// exp(-2 pi i m / lcm) (forward scan phase) in FP32 and as an FP16 hi/lo split, and the inverse
+// exp(-2 pi i m / lcm) (forward scan phase) in FP32 and as an FP16 hi/lo split packed as
+// (re_hi | re_lo << 16, im_hi | im_lo << 16), and the inverse
 // DFT twiddles exp(+2 pi i m / n) for both scan axes.
-__global__ void tables_kernel(float2* tw, uint4* tw16, int lcm, float2* twy, int Sy, float2* twx,
+__global__ void tables_kernel(float2* tw, uint2* tw16, int lcm, float2* twy, int Sy, float2* twx,
                               int Sx) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < lcm) {
@@ -240,12 +241,8 @@ __global__ void tables_kernel(float2* tw, uint4* tw16, int lcm, float2* twy, int
         __half rl = __double2half(re - (double)__half2float(rh));
         __half ih = __double2half(im);
         __half il = __double2half(im - (double)__half2float(ih));
-        uint4 q;
-        q.x = __half_as_ushort(rh);
-        q.y = __half_as_ushort(rl);
-        q.z = __half_as_ushort(ih);
-        q.w = __half_as_ushort(il);
-        tw16[t] = q;
+        tw16[t] = make_uint2((uint32_t)__half_as_ushort(rh) | ((uint32_t)__half_as_ushort(rl) << 16),
+                             (uint32_t)__half_as_ushort(ih) | ((uint32_t)__half_as_ushort(il) << 16));
     }
     if (t < Sy) {
         double s, c;

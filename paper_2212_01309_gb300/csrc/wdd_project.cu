@@ -7,6 +7,9 @@
 // The scan indices of the launch arrive as a by-value parameter block and are stored next to
 // the staged coefficients for the phase accumulation, so a push needs no host-to-device copy.
 //
+// For the split-precision path the kernel also keeps a running maximum of |c| per coefficient
+// (float bits compared as unsigned integers), from which the accumulation picks its scales.
+//
 // Grid: (frames, row blocks).  Each CTA reduces kProjRows detector rows.  When a frame spans more
 // than one row block, every CTA writes its partial coefficients to a scratch slot and the last
 // CTA to arrive (per-frame arrival counter) adds the partials in row-block order, so the result
@@ -47,7 +50,7 @@ project_kernel(const FT* __restrict__ frames, int Ny, int Nx, int Ly, int Lx, in
                const float2* __restrict__ By, const float2* __restrict__ Bx,
                const int2* __restrict__ ktab, float* __restrict__ cpart,
                unsigned* __restrict__ count, float* __restrict__ c_out, int nrb,
-               const IndexBlock ids, int32_t* __restrict__ idx_out) {
+               const IndexBlock ids, int32_t* __restrict__ idx_out, unsigned* __restrict__ colmax) {
     extern __shared__ float sm[];
     const int b = blockIdx.x;
     const int rb = blockIdx.y;
@@ -108,6 +111,7 @@ project_kernel(const FT* __restrict__ frames, int Ny, int Nx, int Ly, int Lx, in
             }
         }
         dst[k] = acc;
+        if (nrb == 1 && colmax) atomicMax(colmax + k, __float_as_uint(fabsf(acc)));
     }
     if (nrb == 1) return;
 
@@ -126,6 +130,7 @@ project_kernel(const FT* __restrict__ frames, int Ny, int Nx, int Ly, int Lx, in
         float acc = 0.f;
         for (int q = 0; q < nrb; ++q) acc += __ldcg(cpart + ((size_t)b * nrb + q) * K + k);
         c_out[(size_t)b * K + k] = acc;
+        if (colmax) atomicMax(colmax + k, __float_as_uint(fabsf(acc)));
     }
     if (threadIdx.x == 0) count[b] = 0u;  // ready for the next launch (stream ordered)
 }
@@ -140,11 +145,11 @@ cudaError_t launch_typed(const wdd_plan* P, const FT* frames, int n, const Index
     if (P->complex_basis) {
         project_kernel<FT, true><<<grid, kThreads, smem, st>>>(
             frames, P->Ny, P->Nx, P->Ly, P->Lx, P->K, P->d_By32, P->d_Bx32, P->d_ktab,
-            P->d_cpart, P->d_count, c_out, P->rb, ids, idx_out);
+            P->d_cpart, P->d_count, c_out, P->rb, ids, idx_out, P->d_colmax);
     } else {
         project_kernel<FT, false><<<grid, kThreads, smem, st>>>(
             frames, P->Ny, P->Nx, P->Ly, P->Lx, P->K, P->d_By32, P->d_Bx32, P->d_ktab,
-            P->d_cpart, P->d_count, c_out, P->rb, ids, idx_out);
+            P->d_cpart, P->d_count, c_out, P->rb, ids, idx_out, P->d_colmax);
     }
     return cudaGetLastError();
 }

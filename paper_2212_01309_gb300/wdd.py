@@ -90,6 +90,8 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "wdd_set_stage_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "wdd_get_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "wdd_check_device": (ctypes.c_int, [ctypes.c_void_p]),
+    "wdd_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64]),
     "wdd_get_hit_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wdd_copy_array": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -257,6 +259,10 @@ class Plan:
         _check(lib().wdd_plan_get_info(self._h, ctypes.byref(pi)), "wdd_plan_get_info")
         return {name: getattr(pi, name) for name, _ in PlanInfo._fields_}
 
+    def check_device(self) -> None:
+        """Raises WddError(ERR_TIMEOUT) if a kernel of this plan gave up a bounded wait."""
+        _check(lib().wdd_check_device(self._h), "wdd_check_device")
+
     STAGES = ("project", "accumulate", "deconvolve", "idft")
 
     def set_stage_timing(self, enable: bool) -> None:
@@ -300,3 +306,8 @@ class Plan:
         if which in ("basis_y", "basis_x") and not cplx_basis:
             out = out.real.copy()
         return out
+
+
+def selftest_bounded_wait(wait_ns: int = 50_000_000) -> int:
+    """Runs the device bounded-wait self test; returns the status code (ERR_TIMEOUT expected)."""
+    return int(lib().wdd_selftest_bounded_wait(int(wait_ns)))
