@@ -153,6 +153,9 @@ __device__ __forceinline__ uint32_t fastmod(uint32_t x, FastMod f) {
     uint64_t low = f.M * (uint64_t)x;
     return (uint32_t)__umul64hi(low, (uint64_t)f.d);
 }
+__device__ __forceinline__ uint32_t fastdiv(uint32_t x, FastMod f) {
+    return (f.d == 1u) ? x : (uint32_t)__umul64hi(f.M, (uint64_t)x);
+}
 
 struct TcArgs {
     const uint32_t* bsplit;   // pre-arranged B operand (see split_coeff_kernel)
@@ -179,9 +182,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     uint64_t* empty = full + kStages;
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-    int* s_sy = reinterpret_cast<int*>(tmem_slot + 4);     // [kStages][kChunk]
-    int* s_sx = s_sy + kStages * kChunk;
-    float* s_scale = reinterpret_cast<float*>(s_sx + kStages * kChunk);   // [NT]
+    float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);   // [NT]
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5;
@@ -232,16 +233,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 }
             }
             if (s_abort) break;
-            // scan coordinates of this stage's frames (one K-step per producer half)
-            int* sy = s_sy + st * kChunk;
-            int* sx = s_sx + st * kChunk;
-            if (row < 16) {
-                int b = it * kChunk + kstep * 16 + row;
-                int s = a.idx[b];
-                sy[kstep * 16 + row] = s / a.Sx;
-                sx[kstep * 16 + row] = s % a.Sx;
+            // scan coordinates of this thread's 16 frames (decoded per thread: no barrier that an
+            // aborting thread could leave its siblings waiting on)
+            uint32_t fsy[16], fsx[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                uint32_t s = (uint32_t)__ldg(a.idx + it * kChunk + kstep * 16 + j);
+                uint32_t q = fastdiv(s, a.mod_x);
+                fsy[j] = q;
+                fsx[j] = s - q * (uint32_t)a.Sx;
             }
-            asm volatile("bar.sync %0, %1;" ::"r"(1 + kstep), "r"(128));
             uint8_t* stg = stage_base + st * stageBytes;
             // two core matrices (8 frames each) along K for this K-step
 #pragma unroll
@@ -252,9 +253,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     uint2 q[2];
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        int j = kstep * 16 + c * 8 + e + u;
-                        uint32_t m = fastmod(vy * (uint32_t)sy[j], a.mod_y) * (uint32_t)a.my +
-                                     fastmod(vx * (uint32_t)sx[j], a.mod_x) * (uint32_t)a.mx;
+                        const int j = c * 8 + e + u;
+                        uint32_t m = fastmod(vy * fsy[j], a.mod_y) * (uint32_t)a.my +
+                                     fastmod(vx * fsx[j], a.mod_x) * (uint32_t)a.mx;
                         if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
                         q[u] = vok ? __ldg(a.tw16 + m) : make_uint2(0u, 0u);
                     }
@@ -339,7 +340,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = warp * 32 + lane;
         const int v = v0 + row;
-        if (ok && !s_abort) {
+        const bool go = __all_sync(0xffffffffu, ok && !s_abort);   // tcgen05.ld needs the whole warp
+        if (go) {
             const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
             for (int c0 = 0; c0 < NT; c0 += 16) {
                 float re[16], im[16];
@@ -439,7 +441,7 @@ int split_tile_n(int K) {
 
 size_t split_smem_bytes(int NT) {
     size_t stage = 4 * (size_t)kATileBytes + 2 * (size_t)NT * kChunk * 2;
-    return 1024 + kStages * stage + 8 * (2 * kStages + 1) + 16 + 2 * 4 * kStages * kChunk + 4 * (size_t)NT;
+    return 1024 + kStages * stage + 8 * (2 * kStages + 1) + 16 + 4 * (size_t)NT;
 }
 
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
