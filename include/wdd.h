@@ -84,12 +84,20 @@ typedef struct {
     double det_center_y;      /* detector zero-frequency pixel; negative = det_y / 2 (integer) */
     double det_center_x;
     int32_t eps_absolute;     /* 1: eps_eff = epsilon; 0: eps_eff = epsilon * max |chi|^2     */
-    int32_t reserved0;
+    int32_t proj_cluster;     /* CTAs per frame in the projection (1, 2, 4 or 8); 0 = automatic */
     int64_t hbm_budget_bytes; /* refuse plans whose device footprint exceeds this; 0 = none   */
+    int32_t overlap_pushes;   /* 1: a push's first projection may start before the previous
+                                 kernel on the stream has finished (programmatic dependent
+                                 launch).  Set it only when no kernel that produces the frames
+                                 runs on the stream right before a push, e.g. frames written by
+                                 a detector DMA or by copies.  Later chunks of one push always
+                                 overlap (their predecessor is the push's own projection). */
+    int32_t reserved1;
 } wdd_params;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
- * N/2, relative epsilon 1e-3.  Geometry fields are zeroed and must be set by the caller. */
+ * N/2, relative epsilon 1e-3, no overlap across pushes.  Geometry fields are zeroed and must be
+ * set by the caller. */
 wdd_status wdd_params_default(wdd_params* p);
 
 typedef struct wdd_plan wdd_plan;

@@ -20,6 +20,7 @@
 
 #include <cuda_fp16.h>
 
+#include "wdd_device.cuh"
 #include "wdd_internal.h"
 
 namespace wdd {
@@ -34,65 +35,6 @@ constexpr int kStages = 3;
 
 // Bytes of one operand tile for one stage: kChunk/16 K-steps of 128 rows x 16 frames (FP16).
 constexpr int kATileBytes = kTileM * kChunk * 2;   // 8 KB
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true when the phase completed, false once wait_ns of wall time have passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t wait_ns) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (unsigned i = 1; i != 0; ++i) {   // also capped at 2^32 polls
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 255u) == 0u && globaltimer_ns() - t0 > wait_ns) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
 // LBO = byte distance between the two core matrices along K, SBO = between 8-row groups.
@@ -165,7 +107,7 @@ struct TcArgs {
     const uint2* tw16;        // [lcm] (re_hi | re_lo << 16, im_hi | im_lo << 16)
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
-    int n_pad, S, K, NT, Sx, lcm, my, mx, stages_total, tmem_cols;
+    int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_in_smem;
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
@@ -183,6 +125,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);   // [NT]
+    uint2* s_tab = reinterpret_cast<uint2*>(
+        (reinterpret_cast<uintptr_t>(s_scale + NT) + 15) & ~uintptr_t(15));   // [lcm] if it fits
+    const uint2* tab = a.tab_in_smem ? s_tab : a.tw16;
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5;
@@ -203,6 +148,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         int k = k0 + t;
         s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
     }
+    if (a.tab_in_smem)
+        for (int t = threadIdx.x; t < a.lcm; t += blockDim.x) s_tab[t] = a.tw16[t];
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -233,18 +180,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 }
             }
             if (s_abort) break;
-            // scan coordinates of this thread's 16 frames (decoded per thread: no barrier that an
-            // aborting thread could leave its siblings waiting on)
-            uint32_t fsy[16], fsx[16];
+            // Phase index of this thread's 16 frames.  m = (vy sy mod Sy) my + (vx sx mod Sx) mx;
+            // when a frame is the raster successor of the previous one, the two residues are
+            // advanced by additions instead of being recomputed (the branch is warp-uniform).
+            const int32_t* ip = a.idx + it * kChunk + kstep * 16;
+            int32_t sv[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                uint32_t s = (uint32_t)__ldg(a.idx + it * kChunk + kstep * 16 + j);
-                uint32_t q = fastdiv(s, a.mod_x);
-                fsy[j] = q;
-                fsx[j] = s - q * (uint32_t)a.Sx;
-            }
+            for (int j = 0; j < 16; ++j) sv[j] = __ldg(ip + j);
+            uint32_t sy = 0, sx = 0, myp = 0, mxp = 0;
             uint8_t* stg = stage_base + st * stageBytes;
-            // two core matrices (8 frames each) along K for this K-step
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 uint32_t rh[4], rl[4], ih[4], il[4];
@@ -254,15 +198,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int j = c * 8 + e + u;
-                        uint32_t m = fastmod(vy * fsy[j], a.mod_y) * (uint32_t)a.my +
-                                     fastmod(vx * fsx[j], a.mod_x) * (uint32_t)a.mx;
+                        if (j > 0 && sv[j] == sv[j - 1] + 1) {
+                            ++sx;
+                            mxp += vx;
+                            if (mxp >= (uint32_t)a.Sx) mxp -= (uint32_t)a.Sx;
+                            if (sx == (uint32_t)a.Sx) {
+                                sx = 0;
+                                mxp = 0;
+                                ++sy;
+                                myp += vy;
+                                if (myp >= (uint32_t)a.Sy) myp -= (uint32_t)a.Sy;
+                            }
+                        } else {
+                            const uint32_t s = (uint32_t)sv[j];
+                            sy = fastdiv(s, a.mod_x);
+                            sx = s - sy * (uint32_t)a.Sx;
+                            myp = fastmod(vy * sy, a.mod_y);
+                            mxp = fastmod(vx * sx, a.mod_x);
+                        }
+                        uint32_t m = myp * (uint32_t)a.my + mxp * (uint32_t)a.mx;
                         if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
-                        q[u] = vok ? __ldg(a.tw16 + m) : make_uint2(0u, 0u);
+                        q[u] = vok ? tab[m] : make_uint2(0u, 0u);
                     }
-                    rh[e / 2] = (q[0].x & 0xFFFFu) | (q[1].x << 16);
-                    rl[e / 2] = (q[0].x >> 16) | (q[1].x & 0xFFFF0000u);
-                    ih[e / 2] = (q[0].y & 0xFFFFu) | (q[1].y << 16);
-                    il[e / 2] = (q[0].y >> 16) | (q[1].y & 0xFFFF0000u);
+                    rh[e / 2] = __byte_perm(q[0].x, q[1].x, 0x5410);
+                    rl[e / 2] = __byte_perm(q[0].x, q[1].x, 0x7632);
+                    ih[e / 2] = __byte_perm(q[0].y, q[1].y, 0x5410);
+                    il[e / 2] = __byte_perm(q[0].y, q[1].y, 0x7632);
                 }
                 const int off = kstep * 4096 + g * 256 + c * 128 + r * 16;
                 *reinterpret_cast<uint4*>(stg + 0 * kATileBytes + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
@@ -441,7 +402,14 @@ int split_tile_n(int K) {
 
 size_t split_smem_bytes(int NT) {
     size_t stage = 4 * (size_t)kATileBytes + 2 * (size_t)NT * kChunk * 2;
-    return 1024 + kStages * stage + 8 * (2 * kStages + 1) + 16 + 4 * (size_t)NT;
+    return 1024 + kStages * stage + 8 * (2 * kStages + 1) + 16 + 4 * (size_t)NT + 16;
+}
+
+// Shared-memory bytes of the phase table when it is kept on chip (0 when it does not fit).
+static size_t split_table_bytes(int NT, int lcm) {
+    const size_t limit = 226 * 1024;
+    const size_t tab = 8 * (size_t)lcm;
+    return split_smem_bytes(NT) + tab <= limit ? tab : 0;
 }
 
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
@@ -472,6 +440,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.K = P->K;
     a.NT = NT;
     a.Sx = P->Sx;
+    a.Sy = P->Sy;
     a.lcm = P->lcm;
     a.my = P->lcm / P->Sy;
     a.mx = P->lcm / P->Sx;
@@ -483,7 +452,9 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
     dim3 grid((P->S + kTileM - 1) / kTileM, Kp / NT);
-    accumulate_tc_kernel<<<grid, kThreadsTC, split_smem_bytes(NT), st>>>(a);
+    const size_t tab = split_table_bytes(NT, P->lcm);
+    a.tab_in_smem = tab > 0 ? 1 : 0;
+    accumulate_tc_kernel<<<grid, kThreadsTC, split_smem_bytes(NT) + tab, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -141,7 +141,6 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += (int64_t)P->S;                                     // mask
     b += 16LL * P->lcm + 8LL * (P->Sy + P->Sx);             // tables
     b += 4LL * P->depth * P->K + 4LL * P->depth;            // staging
-    b += 4LL * P->chunk * P->rb * P->K + 4LL * P->chunk;     // projection partials
     b += 16LL * P->S;                                       // spectrum + DFT scratch
     b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
     return b;
@@ -163,16 +162,23 @@ cudaEvent_t pool_event(wdd_plan* P) {
 template <typename F>
 cudaError_t staged_launch(wdd_plan* P, int stage, int count, F&& launch) {
     cudaEvent_t a = nullptr, b = nullptr;
+    // inside stream capture the events become event-record nodes of the graph
+    unsigned flags = cudaEventRecordDefault;
     if (P->timing) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(P->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            flags = cudaEventRecordExternal;
         a = pool_event(P);
         b = pool_event(P);
-        cudaEventRecord(a, P->stream);
+        cudaError_t er = cudaEventRecordWithFlags(a, P->stream, flags);
+        if (er != cudaSuccess) return er;
     }
     cudaError_t e = launch();
     if (e != cudaSuccess) return e;
     P->launches_total += count;
     if (P->timing) {
-        cudaEventRecord(b, P->stream);
+        cudaError_t er = cudaEventRecordWithFlags(b, P->stream, flags);
+        if (er != cudaSuccess) return er;
         P->timed.push_back({stage, count, a, b});
     }
     return cudaSuccess;
@@ -287,6 +293,8 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     if (p.accum_depth < 0 || p.accum_depth > (1 << 20))
         return fail(WDD_ERR_INVALID_ARG, "accum_depth must be in [0, 2^20]");
     if (p.rank_k <= 0) return fail(WDD_ERR_INVALID_ARG, "rank_k must be positive");
+    if (p.proj_cluster < 0 || p.proj_cluster > 8 || (p.proj_cluster & (p.proj_cluster - 1)))
+        return fail(WDD_ERR_INVALID_ARG, "proj_cluster must be 0, 1, 2, 4 or 8");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -309,7 +317,6 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
         return fail(WDD_ERR_INVALID_ARG, "split precision stages at most 8192 frames");
     }
     P->lcm = std::lcm(P->Sy, P->Sx);
-    P->rb = (P->Ny + kProjRows - 1) / kProjRows;
     cudaGetDevice(&P->device);
 
     // ---- geometry (Sect. 6.3) ------------------------------------------------------------
@@ -374,9 +381,9 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
         // shared-memory footprints of the plan and projection kernels (227 KB per CTA)
         const size_t lim = 227u * 1024u;
         size_t chi = 16u * ((size_t)P->Nx * P->Lx + 8u * P->Nx + 8u * P->Lx);
-        int cw = P->complex_basis ? 2 : 1;
-        size_t proj = 4u * ((size_t)P->Nx * P->Lx * cw + (size_t)kProjRows * P->Nx +
-                            (size_t)kProjRows * P->Lx * cw);
+        P->proj = make_proj_geom(P->Ny, P->Nx, P->Ly, P->Lx, P->K, P->complex_basis,
+                                 std::min(p.max_batch, kLaunchFrames), p.proj_cluster);
+        size_t proj = proj_smem_bytes(P->proj) + 1024;
         size_t tc = p.precision == WDD_PREC_SPLIT ? split_smem_bytes(split_tile_n(P->K)) : 0;
         if (chi > lim || proj > lim || tc > lim) {
             delete P;
@@ -452,8 +459,6 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     WDD_ALLOC(P->d_cstage, (size_t)P->depth_pad * P->K);
     WDD_ALLOC(P->d_idxstage, P->depth_pad);
     WDD_ALLOC(P->d_status, 1);
-    WDD_ALLOC(P->d_cpart, (size_t)P->chunk * P->rb * P->K);
-    WDD_ALLOC(P->d_count, P->chunk);
     WDD_ALLOC(P->d_o, P->S);
     WDD_ALLOC(P->d_tmp, P->S);
     if (p.precision == WDD_PREC_SPLIT) {
@@ -509,7 +514,6 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     if ((e = launch_weights(P, s0))) return cbail(e, "Wiener weights");
     if ((e = launch_tables(P, s0))) return cbail(e, "phase tables");
     if ((e = cudaMemset(P->d_H, 0, 8 * (size_t)P->S * P->K))) return cbail(e, "zero accumulator");
-    if ((e = cudaMemset(P->d_count, 0, 4 * (size_t)P->chunk))) return cbail(e, "zero counters");
     if ((e = cudaMemset(P->d_idxstage, 0, 4 * (size_t)P->depth_pad))) return cbail(e, "zero staging");
     if ((e = cudaMemset(P->d_cstage, 0, 4 * (size_t)P->depth_pad * P->K))) return cbail(e, "zero staging");
     if ((e = cudaMemset(P->d_status, 0, 4))) return cbail(e, "zero status");
@@ -570,7 +574,11 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
     }
     const char* src = nullptr;
     bool pageable = false;
-    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+    bool device_src = false;
+    if (attr.type == cudaMemoryTypeDevice) {
+        src = static_cast<const char*>(frames);
+        device_src = true;
+    } else if (attr.type == cudaMemoryTypeManaged) {
         src = static_cast<const char*>(frames);
     } else if (attr.type == cudaMemoryTypeHost) {
         src = static_cast<const char*>(attr.devicePointer ? attr.devicePointer : frames);
@@ -594,9 +602,11 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
     }
     for (int64_t off = 0; off < n; off += P->chunk) {
         int nb = (int)std::min<int64_t>(P->chunk, n - off);
+        bool flushed = false;
         if (P->staged + nb > P->depth) {
             wdd_status fs = flush(P);
             if (fs != WDD_OK) return fs;
+            flushed = true;
         }
         IndexBlock ids;
         std::memcpy(ids.s, scan_idx + off, sizeof(int32_t) * nb);
@@ -615,7 +625,13 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
         float* c_out = P->d_cstage + (size_t)P->staged * P->K;
         int32_t* i_out = P->d_idxstage + P->staged;
         e = staged_launch(P, WDD_STAGE_PROJECT, 1, [&] {
-            return launch_project(P, fsrc, P->p.frame_dtype, nb, ids, c_out, i_out, st);
+            // overlap with the previous kernel only when that kernel was launched by this call (a
+            // projection of an earlier chunk, or the flush just above, which itself started only
+            // after all earlier work on the stream), or when the caller allowed overlap across
+            // pushes
+            const bool overlap = off > 0 || flushed || P->p.overlap_pushes != 0;
+            return launch_project(P, fsrc, P->p.frame_dtype, nb, device_src, overlap, ids, c_out,
+                                  i_out, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         if (slot) {

@@ -1,0 +1,73 @@
+// Device helpers shared by the kernels of libwdd.so: shared-memory addresses, mbarriers with
+// bounded waits, and 1-D TMA bulk copies.
+#pragma once
+
+#include <stdint.h>
+
+namespace wdd {
+
+static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+static __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+static __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+static __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+static __device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+static __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false once about wait_ns have passed.  The SM
+// cycle counter (cheap to read) measures the time, converted at the maximum SM clock of 2.07 GHz,
+// so at lower clocks the limit is proportionally longer.  The counter is read only after a
+// first burst of polls, so waits that complete quickly never touch it.
+static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t wait_ns) {
+    for (int i = 0; i < 64; ++i)
+        if (mbar_try(bar, parity)) return true;
+    const long long limit = (long long)(wait_ns * 2.07);
+    const long long t0 = clock64();
+    for (unsigned i = 1; i != 0; ++i) {   // also capped at 2^32 polls
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63u) == 0u && clock64() - t0 > limit) return false;
+    }
+    return false;
+}
+
+static __device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+static __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace wdd

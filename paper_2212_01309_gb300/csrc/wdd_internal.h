@@ -8,14 +8,28 @@
 #include <string>
 #include <vector>
 
-#include "../../include/wdd.h"
+#include "wdd.h"  // include/ is on the include path
 
 namespace wdd {
 
 // Threads per block used by most kernels.
 constexpr int kThreads = 256;
-// Detector rows handled by one projection CTA.
-constexpr int kProjRows = 16;
+// Raw frame bytes per projection row block (two blocks are double buffered in shared memory).
+constexpr int kRowBlockBytes = 32 * 1024;
+
+// Launch geometry of the projection kernel (fixed per plan except the frame-type dependent
+// rows per block and the copy path).
+struct ProjGeom {
+    int Ny, Nx, Ly, Lx, K, CW;  // detector, basis sizes, rank, 2 for a complex basis
+    int G;                      // groups of 8 basis rows (re/im counted separately)
+    int P;                      // row parts of the first contraction
+    int SP;                     // slices of the second contraction per coefficient
+    int CS;                     // CTAs per frame (thread-block cluster size, 1..8)
+    int rows_cta;               // detector rows per CTA
+    int RB;                     // rows per shared-memory block
+    int buf_bytes;              // bytes of one of the two row-block buffers
+    int use_tma;                // 1: device frames copied by cp.async.bulk
+};
 // Frames per projection launch; their scan indices travel as a kernel parameter block.
 constexpr int kLaunchFrames = 256;
 struct IndexBlock {
@@ -45,7 +59,7 @@ struct wdd_plan {
     int depth = 0;           // staging depth (frames accumulated per flush)
     int max_batch = 0;
     int chunk = 0;           // frames per projection launch (<= kLaunchFrames)
-    int rb = 0;              // row blocks per frame in the projection
+    wdd::ProjGeom proj{};    // projection launch geometry
     double lambda = 0, R = 0, sigma = 0, eps_eff = 0, cy = 0, cx = 0;
     int n_active = 0;
 
@@ -68,8 +82,6 @@ struct wdd_plan {
     float2* d_twx = nullptr;     // [Sx]
     float* d_cstage = nullptr;   // [depth][K] staged coefficients
     int32_t* d_idxstage = nullptr;  // [depth]
-    float* d_cpart = nullptr;    // [max_batch][rb][2*M] projection partials
-    unsigned* d_count = nullptr; // [max_batch] projection arrival counters
     float2* d_o = nullptr;       // [S] spectrum
     float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
     uint16_t* d_bsplit = nullptr;  // split path: FP16 hi/lo coefficients in the UMMA B layout
@@ -129,9 +141,14 @@ cudaError_t launch_weights(const wdd_plan* P, cudaStream_t st);
 cudaError_t launch_tables(const wdd_plan* P, cudaStream_t st);
 
 // ---- streaming kernels ---------------------------------------------------------------------
+ProjGeom make_proj_geom(int Ny, int Nx, int Ly, int Lx, int K, int complex_basis,
+                        int frames_per_launch, int cluster);
+void proj_set_frame_bytes(ProjGeom& g, int elem_bytes);  // RB and buffer size for a frame type
+size_t proj_smem_bytes(const ProjGeom& g);
+// `overlap`: launch with programmatic stream serialization (see the projection kernel).
 cudaError_t launch_project(const wdd_plan* P, const void* frames, int dtype, int n,
-                           const IndexBlock& idx, float* c_out, int32_t* idx_out,
-                           cudaStream_t st);  // also folds |c| into d_colmax when it is set
+                           bool device_src, bool overlap, const IndexBlock& idx, float* c_out,
+                           int32_t* idx_out, cudaStream_t st);  // also folds |c| into d_colmax
 cudaError_t launch_accumulate_fp32(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                    cudaStream_t st);
 // Device-side waits give up after this long and report WDD_ERR_TIMEOUT.

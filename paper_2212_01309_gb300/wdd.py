@@ -51,8 +51,10 @@ class Params(ctypes.Structure):
         ("det_center_y", ctypes.c_double),
         ("det_center_x", ctypes.c_double),
         ("eps_absolute", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("proj_cluster", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_int64),
+        ("overlap_pushes", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -136,7 +138,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 semiconv_rad, defocus_m=0.0, epsilon=1e-3, rank_k, basis="hg_tensor",
                 precision="fp32", frame_dtype="f32", max_batch=256, accum_depth=0,
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
-                hbm_budget_bytes=0) -> Params:
+                hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False) -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -150,6 +152,8 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.det_center_y, p.det_center_x = det_center_y, det_center_x
     p.eps_absolute = 1 if eps_absolute else 0
     p.hbm_budget_bytes = hbm_budget_bytes
+    p.proj_cluster = proj_cluster
+    p.overlap_pushes = 1 if overlap_pushes else 0
     return p
 
 
