@@ -1,18 +1,22 @@
 // Phase accumulation on the 5th-generation tensor cores (tcgen05, TMEM), split FP16 precision:
 //   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. outer_prod, Algorithm 2)
 //
-// Real form: D_re = Re(E) C and D_im = Im(E) C with one shared B operand C (frames x K).  Each
-// operand is split into FP16 hi + lo parts and three products are accumulated in FP32 TMEM:
-//   D = E_hi c_hi + E_lo c_hi + E_hi c_lo      (the dropped E_lo c_lo is ~2^-22 relative).
-// The coefficients are scaled per column by a power of two before the split so that every
-// column uses the FP16 range fully; the epilogue divides the scale out.
+// Computed transposed, D^T = C^T E^T, so that every UMMA is as wide as the hardware allows:
+//   A operand (M = 128 rows): 64 coefficients, rows 0-63 their FP16 hi parts and rows 64-127 their
+//             lo parts, each column scaled by a power of two first (split_coeff_kernel);
+//   B operand (N = 256 rows): Re and Im of E for 128 scan frequencies, in FP16 hi and lo parts.
+// Two MMAs per 16-frame K-step (B = E_hi, then B = E_lo) accumulate in FP32 TMEM all four products
+// (c_hi + c_lo)(E_hi + E_lo) = c E up to FP16-split rounding (~2^-22 relative); the epilogue adds
+// the hi and lo rows and divides the scale out.
 //
-// Kernel structure (one CTA per 128 scan frequencies x NT coefficients):
-//   warps 0-7  build the A operands (Re/Im, hi/lo of E) for their rows in shared memory, in the
+// Kernel structure (one CTA per 128 scan frequencies x 64 or 128 coefficients):
+//   warps 0-7  build the B operand (Re/Im, hi/lo of E) for their rows in shared memory, in the
 //              no-swizzle K-major core-matrix layout, from the exact integer phase index and an
-//              FP64-built table; warps 0-3 then run the epilogue (tcgen05.ld -> H += D / scale).
-//   warp 8     streams the B operand (hi/lo coefficients, pre-arranged in the same layout by
-//              split_coeff_kernel) into shared memory with 1-D TMA bulk copies.
+//              FP64-built table; they then run the epilogue (tcgen05.ld -> shared-memory tiles ->
+//              coalesced H += (hi + lo) / scale).
+//   warp 8     streams the A operand (split coefficients, pre-arranged in the same layout) into
+//              shared memory with 1-D TMA bulk copies, in a pipeline of its own that runs up to
+//              8 stages ahead, hiding the copy latency.
 //   warp 9     allocates TMEM and one elected lane issues tcgen05.mma; tcgen05.commit frees
 //              each pipeline stage and finally signals the epilogue.
 // Every mbarrier wait is bounded; a wait that runs out records an error code in *status and the
@@ -27,14 +31,13 @@ namespace wdd {
 
 namespace {
 
-constexpr int kTileM = 128;        // scan frequencies per CTA (UMMA M)
+constexpr int kTileV = 128;        // scan frequencies per CTA (Re and Im rows: UMMA N = 256)
 constexpr int kChunk = 32;         // frames per pipeline stage (two UMMA K-steps of 16)
 constexpr int kProducers = 256;    // warps 0-7
 constexpr int kThreadsTC = 320;    // + TMA warp + MMA warp
-constexpr int kStages = 3;
-
-// Bytes of one operand tile for one stage: kChunk/16 K-steps of 128 rows x 16 frames (FP16).
-constexpr int kATileBytes = kTileM * kChunk * 2;   // 8 KB
+constexpr int kEKStepBytes = 2 * kTileV * 16 * 2;   // one K-step of an E operand: 256 rows x 16 frames
+constexpr int kEStageBytes = 2 * 2 * kEKStepBytes;  // hi and lo, two K-steps: 32 KB
+constexpr int kCMTileKStep = 128 * 16 * 2;          // one K-step of a 128-row coefficient tile: 4 KB
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
 // LBO = byte distance between the two core matrices along K, SBO = between 8-row groups.
@@ -100,7 +103,7 @@ __device__ __forceinline__ uint32_t fastdiv(uint32_t x, FastMod f) {
 }
 
 struct TcArgs {
-    const uint32_t* bsplit;   // pre-arranged B operand (see split_coeff_kernel)
+    const uint16_t* csplit;   // pre-arranged A operand (see split_coeff_kernel)
     const float* scale_inv;   // [Kp] 1 / column scale
     unsigned* colmax;         // [K] per-column max |c| (reset here for the next flush)
     const int32_t* idx;       // [n] scan index of each staged frame
@@ -108,38 +111,68 @@ struct TcArgs {
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
     int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_in_smem;
+    int stagesE, stagesC;     // pipeline depths (E: generated phase factors, C: coefficients)
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
 
+// Shared-memory layout of accumulate_tc_kernel (offsets from a 1024-byte aligned base).
+struct TcLayout {
+    size_t e, c, bar, tmem, scale, tab, total;
+};
+__host__ __device__ inline TcLayout tc_layout(int NT, int stagesE, int stagesC, int lcm, int tab) {
+    TcLayout L;
+    const size_t cStage = (size_t)(NT / 64) * 2 * kCMTileKStep;
+    L.e = 0;
+    L.c = L.e + (size_t)stagesE * kEStageBytes;
+    L.bar = L.c + (size_t)stagesC * cStage;
+    L.tmem = L.bar + 8 * (size_t)(2 * stagesE + 2 * stagesC + 1);
+    L.scale = (L.tmem + 16 + 15) & ~size_t(15);
+    L.tab = (L.scale + 4 * (size_t)NT + 15) & ~size_t(15);
+    L.total = L.tab + (tab ? 8 * (size_t)lcm : 0);
+    return L;
+}
+
+// Named barrier among the 256 threads of warps 0-7 (the epilogue phases).
+__device__ __forceinline__ void epilogue_barrier() {
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned carve-up
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NT = a.NT;
-    const int bTileBytes = NT * kChunk * 2;          // one hi or lo B tile per stage
-    const int stageBytes = 4 * kATileBytes + 2 * bTileBytes;
-    uint8_t* stage_base = base;
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + kStages * stageBytes);
-    uint64_t* empty = full + kStages;
-    uint64_t* done = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-    float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);   // [NT]
-    uint2* s_tab = reinterpret_cast<uint2*>(
-        (reinterpret_cast<uintptr_t>(s_scale + NT) + 15) & ~uintptr_t(15));   // [lcm] if it fits
+    const int NT = a.NT;                 // coefficients per CTA (64 or 128)
+    const int MT = NT / 64;              // 128-row coefficient tiles (hi rows 0-63, lo rows 64-127)
+    const int SE = a.stagesE, SC = a.stagesC;
+    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, a.tab_in_smem);
+    const int cStageBytes = MT * 2 * kCMTileKStep;
+    uint8_t* e_base = base + L.e;
+    uint8_t* c_base = base + L.c;
+    uint64_t* fullE = reinterpret_cast<uint64_t*>(base + L.bar);
+    uint64_t* emptyE = fullE + SE;
+    uint64_t* fullC = emptyE + SE;
+    uint64_t* emptyC = fullC + SC;
+    uint64_t* done = emptyC + SC;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
+    float* s_scale = reinterpret_cast<float*>(base + L.scale);
+    uint2* s_tab = reinterpret_cast<uint2*>(base + L.tab);
     const uint2* tab = a.tab_in_smem ? s_tab : a.tw16;
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int v0 = blockIdx.x * kTileM;
+    const int v0 = blockIdx.x * kTileV;
     const int k0 = blockIdx.y * NT;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], kProducers + 1);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < SE; ++s) {
+            mbar_init(&fullE[s], kProducers / 32);   // one arrival per producer warp
+            mbar_init(&emptyE[s], 1);
+        }
+        for (int s = 0; s < SC; ++s) {
+            mbar_init(&fullC[s], 1);
+            mbar_init(&emptyC[s], 1);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -162,167 +195,204 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     const uint32_t tmem = *tmem_slot;
 
     if (warp < 8) {
-        // ---------------- A producers ----------------
-        const int row = threadIdx.x & (kTileM - 1);    // 0..127
+        // ---------------- E producers: phase factors as the B operand (N rows = Re, Im) ----
+        const int row = threadIdx.x & (kTileV - 1);    // 0..127
         const int kstep = threadIdx.x >> 7;            // 0..1: which 16-frame K-step of a stage
         const int v = v0 + row;
         const bool vok = v < a.S;
         const uint32_t vy = vok ? (uint32_t)(v / a.Sx) : 0u;
         const uint32_t vx = vok ? (uint32_t)(v % a.Sx) : 0u;
-        const int g = row >> 3, r = row & 7;
+        const int g_re = row >> 3, g_im = 16 + (row >> 3), r = row & 7;
+        // phase steps j * vx * mx mod lcm between a frame and its j-th successor in a scan row
+        uint32_t dxj[16];
+        {
+            const uint32_t dx = vx * (uint32_t)a.mx;   // < lcm
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                dxj[j] = acc;
+                acc += dx;
+                if (acc >= (uint32_t)a.lcm) acc -= (uint32_t)a.lcm;
+            }
+        }
         for (int it = 0; it < a.stages_total; ++it) {
-            const int st = it % kStages;
-            if (it >= kStages) {
-                if (!mbar_wait(&empty[st], ((it / kStages) - 1) & 1, a.wait_ns)) {
+            const int st = it % SE;
+            // one lane per warp waits for the stage to be free and tells its warp
+            int ok = 1;
+            if (lane == 0) {
+                if (it >= SE && !mbar_wait(&emptyE[st], ((it / SE) - 1) & 1, a.wait_ns)) {
                     atomicExch(a.status, 1u);
                     s_abort = 1;
-                    break;
+                }
+                ok = !s_abort;
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            // Phase index of this thread's 16 frames, m = (vy sy mod Sy) my + (vx sx mod Sx) mx
+            // (mod lcm).  Fast path, decided per K-step (warp-uniform): the 16 frames are
+            // consecutive positions of one scan row, so m advances by dx = vx mx per frame.
+            // Otherwise each frame's index is decoded on its own.
+            const int32_t* ip = a.idx + it * kChunk + kstep * 16;
+            const int32_t s_first = __ldg(ip), s_last = __ldg(ip + 15);
+            uint32_t mm[16];
+            {
+                const uint32_t s0 = (uint32_t)s_first;
+                const uint32_t sy0 = fastdiv(s0, a.mod_x);
+                const uint32_t sx0 = s0 - sy0 * (uint32_t)a.Sx;
+                if (s_last == s_first + 15 && sx0 + 15u < (uint32_t)a.Sx) {
+                    uint32_t m = fastmod(vy * sy0, a.mod_y) * (uint32_t)a.my +
+                                 fastmod(vx * sx0, a.mod_x) * (uint32_t)a.mx;
+                    if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {   // independent of each other: no serial chain
+                        const uint32_t mj = m + dxj[j];
+                        mm[j] = (mj >= (uint32_t)a.lcm) ? mj - (uint32_t)a.lcm : mj;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t s = (uint32_t)__ldg(ip + j);
+                        const uint32_t sy = fastdiv(s, a.mod_x);
+                        const uint32_t sx = s - sy * (uint32_t)a.Sx;
+                        uint32_t m = fastmod(vy * sy, a.mod_y) * (uint32_t)a.my +
+                                     fastmod(vx * sx, a.mod_x) * (uint32_t)a.mx;
+                        mm[j] = (m >= (uint32_t)a.lcm) ? m - (uint32_t)a.lcm : m;
+                    }
                 }
             }
-            if (s_abort) break;
-            // Phase index of this thread's 16 frames.  m = (vy sy mod Sy) my + (vx sx mod Sx) mx;
-            // when a frame is the raster successor of the previous one, the two residues are
-            // advanced by additions instead of being recomputed (the branch is warp-uniform).
-            const int32_t* ip = a.idx + it * kChunk + kstep * 16;
-            int32_t sv[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) sv[j] = __ldg(ip + j);
-            uint32_t sy = 0, sx = 0, myp = 0, mxp = 0;
-            uint8_t* stg = stage_base + st * stageBytes;
+            uint8_t* ehi = e_base + (size_t)st * kEStageBytes + kstep * kEKStepBytes;
+            uint8_t* elo = ehi + 2 * kEKStepBytes;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
+                uint2 q[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) q[e] = vok ? tab[mm[c * 8 + e]] : make_uint2(0u, 0u);
                 uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    uint2 q[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int j = c * 8 + e + u;
-                        if (j > 0 && sv[j] == sv[j - 1] + 1) {
-                            ++sx;
-                            mxp += vx;
-                            if (mxp >= (uint32_t)a.Sx) mxp -= (uint32_t)a.Sx;
-                            if (sx == (uint32_t)a.Sx) {
-                                sx = 0;
-                                mxp = 0;
-                                ++sy;
-                                myp += vy;
-                                if (myp >= (uint32_t)a.Sy) myp -= (uint32_t)a.Sy;
-                            }
-                        } else {
-                            const uint32_t s = (uint32_t)sv[j];
-                            sy = fastdiv(s, a.mod_x);
-                            sx = s - sy * (uint32_t)a.Sx;
-                            myp = fastmod(vy * sy, a.mod_y);
-                            mxp = fastmod(vx * sx, a.mod_x);
-                        }
-                        uint32_t m = myp * (uint32_t)a.my + mxp * (uint32_t)a.mx;
-                        if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
-                        q[u] = vok ? tab[m] : make_uint2(0u, 0u);
-                    }
-                    rh[e / 2] = __byte_perm(q[0].x, q[1].x, 0x5410);
-                    rl[e / 2] = __byte_perm(q[0].x, q[1].x, 0x7632);
-                    ih[e / 2] = __byte_perm(q[0].y, q[1].y, 0x5410);
-                    il[e / 2] = __byte_perm(q[0].y, q[1].y, 0x7632);
+                for (int e = 0; e < 4; ++e) {
+                    rh[e] = __byte_perm(q[2 * e].x, q[2 * e + 1].x, 0x5410);
+                    rl[e] = __byte_perm(q[2 * e].x, q[2 * e + 1].x, 0x7632);
+                    ih[e] = __byte_perm(q[2 * e].y, q[2 * e + 1].y, 0x5410);
+                    il[e] = __byte_perm(q[2 * e].y, q[2 * e + 1].y, 0x7632);
                 }
-                const int off = kstep * 4096 + g * 256 + c * 128 + r * 16;
-                *reinterpret_cast<uint4*>(stg + 0 * kATileBytes + off) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                *reinterpret_cast<uint4*>(stg + 1 * kATileBytes + off) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                *reinterpret_cast<uint4*>(stg + 2 * kATileBytes + off) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                *reinterpret_cast<uint4*>(stg + 3 * kATileBytes + off) = make_uint4(il[0], il[1], il[2], il[3]);
+                const int o_re = g_re * 256 + c * 128 + r * 16;
+                const int o_im = g_im * 256 + c * 128 + r * 16;
+                *reinterpret_cast<uint4*>(ehi + o_re) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                *reinterpret_cast<uint4*>(ehi + o_im) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                *reinterpret_cast<uint4*>(elo + o_re) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                *reinterpret_cast<uint4*>(elo + o_im) = make_uint4(il[0], il[1], il[2], il[3]);
             }
-            fence_async_smem();
-            mbar_arrive(&full[st]);
+            fence_async_smem();    // this thread's stores -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullE[st]);
         }
     } else if (warp == 8) {
-        // ---------------- B loader (TMA) ----------------
+        // ---------------- C loader (TMA), running up to SC stages ahead ----------------
         if (lane == 0) {
-            const uint8_t* src = reinterpret_cast<const uint8_t*>(a.bsplit) +
-                                 (size_t)blockIdx.y * a.stages_total * 2 * bTileBytes;
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
+                                 (size_t)blockIdx.y * a.stages_total * cStageBytes;
             for (int it = 0; it < a.stages_total; ++it) {
-                const int st = it % kStages;
-                if (it >= kStages && !mbar_wait(&empty[st], ((it / kStages) - 1) & 1, a.wait_ns)) {
+                const int sc = it % SC;
+                if (it >= SC && !mbar_wait(&emptyC[sc], ((it / SC) - 1) & 1, a.wait_ns)) {
                     atomicExch(a.status, 2u);
                     s_abort = 1;
                     break;
                 }
                 if (s_abort) break;
-                uint8_t* dst = stage_base + st * stageBytes + 4 * kATileBytes;
-                mbar_arrive_tx(&full[st], 2 * bTileBytes);
-                tma_load_1d(dst, src + (size_t)it * 2 * bTileBytes, 2 * bTileBytes, &full[st]);
+                mbar_arrive_tx(&fullC[sc], cStageBytes);
+                tma_load_1d(c_base + (size_t)sc * cStageBytes, src + (size_t)it * cStageBytes,
+                            cStageBytes, &fullC[sc]);
             }
         }
     } else {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer: D_j[coefficient row][Re v | Im v] --------------------
         if (lane == 0) {
-            const uint32_t idesc = instr_desc(kTileM, NT);
-            const uint32_t d_re = tmem, d_im = tmem + (uint32_t)NT;
+            const uint32_t idesc = instr_desc(128, 2 * kTileV);
             uint32_t acc = 0;
-            bool ok = true;
             for (int it = 0; it < a.stages_total; ++it) {
-                const int st = it % kStages;
-                if (!mbar_wait(&full[st], (it / kStages) & 1, a.wait_ns)) {
+                const int st = it % SE, sc = it % SC;
+                if (!mbar_wait(&fullC[sc], (it / SC) & 1, a.wait_ns) ||
+                    !mbar_wait(&fullE[st], (it / SE) & 1, a.wait_ns)) {
                     atomicExch(a.status, 3u);
                     s_abort = 1;
-                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sb = smem_u32(stage_base + st * stageBytes);
+                const uint32_t se = smem_u32(e_base + (size_t)st * kEStageBytes);
+                const uint32_t sca = smem_u32(c_base + (size_t)sc * cStageBytes);
 #pragma unroll
                 for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    const uint32_t aoff = ks * 4096;
-                    const uint64_t a_rh = smem_desc(sb + 0 * kATileBytes + aoff, 128, 256);
-                    const uint64_t a_rl = smem_desc(sb + 1 * kATileBytes + aoff, 128, 256);
-                    const uint64_t a_ih = smem_desc(sb + 2 * kATileBytes + aoff, 128, 256);
-                    const uint64_t a_il = smem_desc(sb + 3 * kATileBytes + aoff, 128, 256);
-                    const uint32_t bb = sb + 4 * kATileBytes + ks * (NT * 32);
-                    const uint64_t b_h = smem_desc(bb, 128, 256);
-                    const uint64_t b_l = smem_desc(bb + bTileBytes, 128, 256);
-                    mma_f16(d_re, a_rh, b_h, idesc, acc);
-                    mma_f16(d_re, a_rl, b_h, idesc, 1u);
-                    mma_f16(d_re, a_rh, b_l, idesc, 1u);
-                    mma_f16(d_im, a_ih, b_h, idesc, acc);
-                    mma_f16(d_im, a_il, b_h, idesc, 1u);
-                    mma_f16(d_im, a_ih, b_l, idesc, 1u);
+                    const uint64_t e_h = smem_desc(se + ks * kEKStepBytes, 128, 256);
+                    const uint64_t e_l = smem_desc(se + (2 + ks) * kEKStepBytes, 128, 256);
+                    for (int j = 0; j < MT; ++j) {
+                        const uint64_t cd = smem_desc(sca + (j * 2 + ks) * kCMTileKStep, 128, 256);
+                        const uint32_t d = tmem + (uint32_t)(j * 2 * kTileV);
+                        mma_f16(d, cd, e_h, idesc, acc);
+                        mma_f16(d, cd, e_l, idesc, 1u);
+                    }
                     acc = 1u;
                 }
-                mma_commit(&empty[st]);   // frees the stage once these MMAs have read it
+                mma_commit(&emptyE[st]);   // free both stages once these MMAs have read them
+                mma_commit(&emptyC[sc]);
             }
             mma_commit(done);              // all issued MMAs complete -> epilogue
-            (void)ok;
         }
     }
 
-    // ---------------- epilogue: warps 0-3 own TMEM lanes 0-127 ----------------
-    if (warp < 4) {
-        const bool ok = mbar_wait(done, 0, a.wait_ns);
-        if (!ok) atomicExch(a.status, 4u);
+    // ---------------- epilogue: warps 0-7 ----------------
+    // TMEM lane = coefficient row (0-63: hi part, 64-127: lo part); column = Re v | Im v.
+    // Warps whose lane quarter holds hi rows write tile T_hi[v][k], the others T_lo[v][k]
+    // (both in the freed E stage buffers), then all eight warps add T_hi + T_lo, scale and
+    // update H with whole 128-byte row segments.
+    if (warp < 8) {
+        int ok = 1;
+        if (lane == 0) {
+            ok = mbar_wait(done, 0, a.wait_ns) ? 1 : 0;
+            if (!ok) atomicExch(a.status, 4u);
+            ok = ok && !s_abort;
+        }
+        const bool go = __shfl_sync(0xffffffffu, ok, 0) != 0;   // tcgen05.ld needs the whole warp
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = warp * 32 + lane;
-        const int v = v0 + row;
-        const bool go = __all_sync(0xffffffffu, ok && !s_abort);   // tcgen05.ld needs the whole warp
-        if (go) {
-            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-            for (int c0 = 0; c0 < NT; c0 += 16) {
-                float re[16], im[16];
-                tmem_ld16(lane_addr + (uint32_t)c0, re);
-                tmem_ld16(lane_addr + (uint32_t)(NT + c0), im);
-                if (v < a.S) {
-                    float2* h = a.H + (size_t)v * a.K + k0 + c0;
+        const int quarter = warp & 3;                 // TMEM lanes 32 q .. 32 q + 31
+        const int half = warp >> 2;                   // which half of the v columns
+        const int krow = (quarter & 1) * 32 + lane;   // coefficient within the m-tile
+        float2* T = reinterpret_cast<float2*>(e_base) + (size_t)(quarter >> 1) * kTileV * 64;
+        for (int j = 0; j < MT; ++j) {
+            if (go) {
+                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(j * 2 * kTileV);
+                for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+                    float re[16], im[16];
+                    tmem_ld16(lane_addr + (uint32_t)c0, re);
+                    tmem_ld16(lane_addr + (uint32_t)(kTileV + c0), im);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        int k = k0 + c0 + i;
+                    for (int i = 0; i < 16; ++i) T[(size_t)(c0 + i) * 64 + krow] = make_float2(re[i], im[i]);
+                }
+            }
+            epilogue_barrier();
+            if (go) {
+                const float2* Thi = reinterpret_cast<const float2*>(e_base);
+                const float2* Tlo = Thi + (size_t)kTileV * 64;
+                for (int vr = warp; vr < kTileV; vr += 8) {
+                    const int vv = v0 + vr;
+                    if (vv >= a.S) continue;
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int kl = hh * 32 + lane;
+                        const int k = k0 + j * 64 + kl;
                         if (k < a.K) {
-                            float sc = s_scale[c0 + i];
-                            float2 hv = h[i];
-                            hv.x = fmaf(re[i], sc, hv.x);
-                            hv.y = fmaf(im[i], sc, hv.y);
-                            h[i] = hv;
+                            const float2 x = Thi[(size_t)vr * 64 + kl], y = Tlo[(size_t)vr * 64 + kl];
+                            const float sc = s_scale[j * 64 + kl];
+                            float2* h = a.H + (size_t)vv * a.K + k;
+                            float2 hv = *h;
+                            hv.x = fmaf(x.x + y.x, sc, hv.x);
+                            hv.y = fmaf(x.y + y.y, sc, hv.y);
+                            *h = hv;
                         }
                     }
                 }
             }
+            epilogue_barrier();
         }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0)
@@ -337,9 +407,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 }
 
 // Splits the staged FP32 coefficients into FP16 hi/lo parts with a power-of-two scale per column
-// and writes them in the B-operand layout of accumulate_tc_kernel:
-//   [k-tile][stage][hi|lo][K-step][row group kk/8][core matrix b/8 % 2][kk % 8][b % 8]
-// Frames beyond n and columns beyond K are zero.  One thread per (frame pair, column).
+// and writes them as the A operand of accumulate_tc_kernel:
+//   [k-tile][stage][m-tile][K-step][row group][core matrix b/8 % 2][row % 8][b % 8]
+// where an m-tile holds 64 coefficients, rows 0-63 their hi parts and rows 64-127 their lo
+// parts.  Frames beyond n and coefficients beyond K are zero.  One thread per (frame, column).
 __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
                                    int n, int n_pad, int K, int Kp, int NT) {
@@ -351,20 +422,24 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
     int e = 0;
     if (cm > 0.f) frexpf(cm, &e);
     const float sc = (cm > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
-    if (b == 0 && kk < Kp) scale_inv[kk] = (kk < K && cm > 0.f) ? ldexpf(1.f, e - 14) : 0.f;
-    float x = (b < n && kk < K) ? c[(size_t)b * K + kk] * sc : 0.f;
-    __half hi = __float2half_rn(x);
-    __half lo = __float2half_rn(x - __half2float(hi));
+    if (b == 0) scale_inv[kk] = (kk < K && cm > 0.f) ? ldexpf(1.f, e - 14) : 0.f;
+    const float x = (b < n && kk < K) ? c[(size_t)b * K + kk] * sc : 0.f;
+    const __half hi = __float2half_rn(x);
+    const __half lo = __float2half_rn(x - __half2float(hi));
     const int ktile = kk / NT, kl = kk % NT;
+    const int mtile = kl / 64, km = kl % 64;
+    const int MT = NT / 64;
     const int stage = b / kChunk, bs = b % kChunk;
     const int ks = bs / 16, bk = bs % 16;
     const int stages_total = n_pad / kChunk;
-    const size_t bTile = (size_t)NT * kChunk;                 // halves per hi or lo tile
-    const size_t base = ((size_t)ktile * stages_total + stage) * 2 * bTile;
-    const size_t within = (size_t)ks * NT * 16 + (size_t)(kl >> 3) * 128 + (size_t)(bk >> 3) * 64 +
-                          (size_t)(kl & 7) * 8 + (bk & 7);
-    out[base + within] = __half_as_ushort(hi);
-    out[base + bTile + within] = __half_as_ushort(lo);
+    const size_t stage_halves = (size_t)MT * 2 * (kCMTileKStep / 2);
+    const size_t base = ((size_t)ktile * stages_total + stage) * stage_halves +
+                        (size_t)(mtile * 2 + ks) * (kCMTileKStep / 2);
+    const int rh = km, rl = 64 + km;
+    const size_t in_hi = (size_t)(rh >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rh & 7) * 8 + (bk & 7);
+    const size_t in_lo = (size_t)(rl >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rl & 7) * 8 + (bk & 7);
+    out[base + in_hi] = __half_as_ushort(hi);
+    out[base + in_lo] = __half_as_ushort(lo);
 }
 
 // Exercises the bounded mbarrier wait on a barrier that nothing arrives on: the wait must give
@@ -395,21 +470,31 @@ cudaError_t prepare_split_kernels() {
     return allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel));
 }
 
-int split_tile_n(int K) {
-    int Kp = (K + 15) / 16 * 16;
-    return Kp <= 256 ? Kp : 256;
+// Coefficients per CTA: 64 (one hi/lo m-tile) or 128 (two).
+int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
+
+// Pipeline depths for a tile width NT within the shared-memory budget.  The E region must hold
+// the two epilogue tiles (128 KB), so it keeps 4 stages; C takes what is left, up to 8.
+static void split_stages(int NT, int lcm, int* se, int* sc, int* tab) {
+    const size_t limit = 226 * 1024 - 1024;   // dynamic bytes after the alignment slack
+    const int E = 4;
+    int C = 8;
+    while (C > 2 && tc_layout(NT, E, C, lcm, 0).total > limit) --C;
+    *se = E;
+    *sc = C;
+    *tab = tc_layout(NT, E, C, lcm, 1).total <= limit ? 1 : 0;
 }
 
 size_t split_smem_bytes(int NT) {
-    size_t stage = 4 * (size_t)kATileBytes + 2 * (size_t)NT * kChunk * 2;
-    return 1024 + kStages * stage + 8 * (2 * kStages + 1) + 16 + 4 * (size_t)NT + 16;
+    int E, C, T;
+    split_stages(NT, 1, &E, &C, &T);
+    return 1024 + tc_layout(NT, E, C, 1, 0).total;
 }
 
-// Shared-memory bytes of the phase table when it is kept on chip (0 when it does not fit).
-static size_t split_table_bytes(int NT, int lcm) {
-    const size_t limit = 226 * 1024;
-    const size_t tab = 8 * (size_t)lcm;
-    return split_smem_bytes(NT) + tab <= limit ? tab : 0;
+size_t split_coeff_bytes(int K, int depth_pad) {
+    const int NT = split_tile_n(K);
+    const int Kp = (K + NT - 1) / NT * NT;
+    return (size_t)Kp * depth_pad * 2 * 2;   // hi and lo halves
 }
 
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
@@ -421,14 +506,14 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     if (n_pad > P->depth_pad) return cudaErrorInvalidValue;
     // 1. split the coefficients (per-column scale from the projection's running max)
     {
-        size_t total = (size_t)n_pad * Kp;
+        const size_t total = (size_t)n_pad * Kp;
         split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
             c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, n, n_pad,
             P->K, Kp, NT);
     }
     // 2. tensor-core accumulation
     TcArgs a;
-    a.bsplit = reinterpret_cast<const uint32_t*>(P->d_bsplit);
+    a.csplit = reinterpret_cast<const uint16_t*>(P->d_bsplit);
     a.scale_inv = P->d_scale_inv;
     a.colmax = P->d_colmax;
     a.idx = idx;
@@ -445,16 +530,14 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.my = P->lcm / P->Sy;
     a.mx = P->lcm / P->Sx;
     a.stages_total = n_pad / kChunk;
-    int cols = 32;
-    while (cols < 2 * NT) cols <<= 1;
-    a.tmem_cols = cols;
+    a.tmem_cols = 2 * kTileV * (NT / 64);   // 256 or 512 columns
     a.wait_ns = kDeviceWaitNs;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
-    dim3 grid((P->S + kTileM - 1) / kTileM, Kp / NT);
-    const size_t tab = split_table_bytes(NT, P->lcm);
-    a.tab_in_smem = tab > 0 ? 1 : 0;
-    accumulate_tc_kernel<<<grid, kThreadsTC, split_smem_bytes(NT) + tab, st>>>(a);
+    split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_in_smem);
+    const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_in_smem).total;
+    dim3 grid((P->S + kTileV - 1) / kTileV, Kp / NT);
+    accumulate_tc_kernel<<<grid, kThreadsTC, smem, st>>>(a);
     return cudaGetLastError();
 }
 

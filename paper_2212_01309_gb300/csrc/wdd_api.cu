@@ -464,7 +464,7 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     if (p.precision == WDD_PREC_SPLIT) {
         int NT = split_tile_n(P->K);
         int Kp = (P->K + NT - 1) / NT * NT;
-        WDD_ALLOC(P->d_bsplit, (size_t)2 * Kp * P->depth_pad);
+        WDD_ALLOC(P->d_bsplit, split_coeff_bytes(P->K, P->depth_pad) / 2);
         WDD_ALLOC(P->d_scale_inv, Kp);
         WDD_ALLOC(P->d_colmax, P->K);
     }

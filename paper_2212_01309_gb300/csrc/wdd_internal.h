@@ -84,7 +84,7 @@ struct wdd_plan {
     int32_t* d_idxstage = nullptr;  // [depth]
     float2* d_o = nullptr;       // [S] spectrum
     float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
-    uint16_t* d_bsplit = nullptr;  // split path: FP16 hi/lo coefficients in the UMMA B layout
+    uint16_t* d_bsplit = nullptr;  // split path: FP16 hi/lo coefficients in the UMMA A layout
     float* d_scale_inv = nullptr;  // split path: [Kp] inverse power-of-two column scales
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
@@ -156,6 +156,7 @@ constexpr uint64_t kDeviceWaitNs = 2000000000ull;
 bool split_path_available();
 int split_tile_n(int K);
 size_t split_smem_bytes(int NT);
+size_t split_coeff_bytes(int K, int depth_pad);   // bytes of the split coefficient operand
 cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cudaStream_t st);
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st);

@@ -2,7 +2,7 @@
 //   o_v = sum_k W_v[k] H[v, k]                 (Hadamard product with K_v, sum of all elements)
 //   O   = conj( IDFT2( o / sqrt(o_0) ) )        (numpy ifft2 normalisation 1/S)
 //   phase = atan2(Im O, Re O)
-// The deconvolution reads H and W once (HBM bound) and accumulates in FP64; the inverse DFT runs
+// The deconvolution reads H and W once (HBM bound); the inverse DFT runs
 // row-column on the S_y x S_x spectrum with exact integer twiddle indices.
 
 #include "wdd_internal.h"
@@ -11,7 +11,8 @@ namespace wdd {
 
 namespace {
 
-// one warp per scan frequency
+// One warp per scan frequency.  FP32 with four independent partial sums per lane, added in a
+// fixed order (FP64 arithmetic is slow on this part and K <= 4096 terms need no more).
 __global__ void deconvolve_kernel(const float2* __restrict__ W, const float2* __restrict__ H,
                                   float2* __restrict__ o, int S, int K) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -19,19 +20,22 @@ __global__ void deconvolve_kernel(const float2* __restrict__ W, const float2* __
     if (warp >= S) return;
     const float2* w = W + (size_t)warp * K;
     const float2* h = H + (size_t)warp * K;
-    double re = 0.0, im = 0.0;
-    for (int k = lane; k < K; k += 32) {
-        float2 a = __ldg(w + k);
-        float2 b = __ldcg(h + k);
-        re += (double)a.x * b.x - (double)a.y * b.y;
-        im += (double)a.x * b.y + (double)a.y * b.x;
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    int k = lane, q = 0;
+    for (; k < K; k += 32, q = (q + 1) & 3) {
+        const float2 a = __ldg(w + k);
+        const float2 b = __ldcg(h + k);
+        re[q] = fmaf(a.x, b.x, fmaf(-a.y, b.y, re[q]));
+        im[q] = fmaf(a.x, b.y, fmaf(a.y, b.x, im[q]));
     }
+    float sr = (re[0] + re[1]) + (re[2] + re[3]);
+    float si = (im[0] + im[1]) + (im[2] + im[3]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, off);
-        im += __shfl_xor_sync(0xffffffffu, im, off);
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
     }
-    if (lane == 0) o[warp] = make_float2((float)re, (float)im);
+    if (lane == 0) o[warp] = make_float2(sr, si);
 }
 
 // 1 / sqrt(z) with the principal square root; 1 when z == 0.  The root is formed without
