@@ -46,6 +46,24 @@ def _env_int(name, default):
         return default
 
 
+def _traffic(stage: str):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu record, or None when
+    the kernel's source has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(stage)
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+        return rec
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -347,8 +365,14 @@ def main(argv=None) -> int:
     elif dom == "project":
         bpl = B * frames_bytes
         ach = bpl / (ms_launch * 1e-3) / 1e9
+        tr = _traffic("project")
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": ach / peaks["hbm"], "traffic": None}
+                "frac": ach / peaks["hbm"],
+                "traffic": (tr["bytes_per_launch"] * B / tr["frames_per_launch"]) if tr else None,
+                "algorithmic_bytes": bpl,
+                "note": f"algorithmic bytes = {B} frames x {frames_bytes} B; duration from events "
+                        f"around each launch (serialised; launches overlap in the timed step); "
+                        f"peak = {peaks['src']} copy bandwidth"}
     else:
         bpl = 16.0 * S * K
         ach = bpl / (ms_launch * 1e-3) / 1e9
@@ -356,6 +380,19 @@ def main(argv=None) -> int:
                 "frac": ach / peaks["hbm"], "traffic": None}
     roof["kernel"] = dom
     roof["launch_ms"] = ms_launch
+    # the tensor-core accumulation, whatever the dominant kernel
+    acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1])
+    acc_alg = 4.0 * S * K * ACCUM_DEPTH / (acc_ms * 1e-3) / 1e12
+    roof_acc = {"bound": "tensor", "kernel": "split_coeff + accumulate_tc" if path == "split"
+                else "accumulate_fp32", "launch_ms": acc_ms,
+                "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * (4 if path == "split" else 1),
+                "peak": peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac_algorithmic": acc_alg / (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),
+                "frac_executed": acc_alg * (4 if path == "split" else 1) /
+                                 (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),
+                "note": "algorithmic 4 S K flops per frame; the split path executes 4x that "
+                        "(hi/lo on both operands, Re and Im); peak = measured bf16 dense "
+                        "(FP16 same rate)"}
 
     # ---- CPU baseline (rank 0, N = 1) -------------------------------------------------------
     cpu = None
@@ -389,6 +426,7 @@ def main(argv=None) -> int:
                            "snapshot_every": LATENCY_SNAPSHOT_EVERY},
             "stage_ms_per_step": stage_ms,
             "roofline": roof,
+            "roofline_accumulate": roof_acc,
             "cpu_baseline": cpu,
             "e2e": {"value": S * world / (ms_e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(S * frames_bytes + 4 * S),
