@@ -204,6 +204,33 @@ wdd_status wdd_check_device(wdd_plan* plan);
  * (the expected result), WDD_OK if it did not, WDD_ERR_CUDA on a CUDA error. */
 wdd_status wdd_selftest_bounded_wait(int64_t wait_ns);
 
+/* Reconstruction for callers that must not allocate device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc: code that runs while a CUDA graph is being captured (allocation is not a legal
+ * stream-capture operation), real-time acquisition threads that must not block on the
+ * allocator (which may synchronise the whole device), and applications whose device memory is
+ * fixed up front by a memory pool or budget that this library must not grow.
+ *
+ * It computes the same result as wdd_snapshot from a plan's Wiener weights and accumulator:
+ * o_v = sum_k W_v[k] H[v,k], O = conj(IFFT2(o / sqrt(o_0))) (numpy ifft2 normalisation),
+ * phase = atan2(Im O, Re O), with the same kernels.  The caller passes everything:
+ *   weights  device complex64 [scan_y * scan_x][rank_k] (W, e.g. read with WDD_ARRAY_WEIGHTS)
+ *   accum    device complex64 [scan_y * scan_x][rank_k] (H, e.g. WDD_ARRAY_ACCUM)
+ *   obj      device complex64 [scan_y][scan_x] output;  phase: device f32 [scan_y][scan_x] or NULL
+ * Its working memory (spectrum, inverse-DFT intermediate, twiddle tables: 16 S + 8 (S_y + S_x)
+ * bytes) lives in a fixed 8 MiB array compiled into the library, held on every GPU that loads
+ * it until the process exits; scans needing more (above about 524,000 positions) are rejected
+ * with WDD_ERR_INVALID_ARG before anything is enqueued.
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array and every call
+ * writes all of the scratch it reads, so nothing needs clearing, but calls whose work may
+ * overlap on the GPU (different streams without ordering) race on it.
+ * Errors: INVALID_ARG (NULL, sizes, scratch too small), CUDA. */
+wdd_status wdd_reconstruct_noalloc(const void* weights, const void* accum, int32_t scan_y,
+                                   int32_t scan_x, int32_t rank_k, void* obj, float* phase,
+                                   wdd_stream_t stream);
+
 /* Copies the per-position hit counts (uint32 [S], exact host bookkeeping) into host memory. */
 wdd_status wdd_get_hit_counts(const wdd_plan* plan, uint32_t* host_out, int64_t n);
 

@@ -757,6 +757,35 @@ wdd_status wdd_selftest_bounded_wait(int64_t wait_ns) {
     return WDD_OK;
 }
 
+wdd_status wdd_reconstruct_noalloc(const void* weights, const void* accum, int32_t scan_y,
+                                   int32_t scan_x, int32_t rank_k, void* obj, float* phase,
+                                   wdd_stream_t stream) {
+    if (!weights || !accum || !obj)
+        return fail(WDD_ERR_INVALID_ARG, "weights, accum and obj must not be NULL");
+    if (scan_y <= 0 || scan_x <= 0 || rank_k <= 0 || scan_y > 4096 || scan_x > 4096)
+        return fail(WDD_ERR_INVALID_ARG, "scan sizes must be in [1, 4096] and rank_k positive");
+    const size_t S = (size_t)scan_y * scan_x;
+    const size_t need = 16 * S + 8 * ((size_t)scan_y + scan_x);
+    if (need > noalloc_scratch_limit()) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "scan %d x %d needs %zu bytes of scratch; the built-in scratch holds %zu "
+                      "(at most about 524,000 scan positions)",
+                      scan_y, scan_x, need, noalloc_scratch_limit());
+        return fail(WDD_ERR_INVALID_ARG, buf);
+    }
+    int dev = 0;
+    WDD_CUDA(cudaGetDevice(&dev));
+    void* scratch = nullptr;
+    WDD_CUDA(noalloc_scratch(dev, &scratch));
+    cudaError_t e = launch_reconstruct_noalloc(scratch, static_cast<const float2*>(weights),
+                                               static_cast<const float2*>(accum), scan_y, scan_x,
+                                               rank_k, static_cast<float2*>(obj), phase,
+                                               static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "reconstruction without allocation");
+    return WDD_OK;
+}
+
 wdd_status wdd_get_hit_counts(const wdd_plan* P, uint32_t* host_out, int64_t n) {
     if (!P || !host_out) return fail(WDD_ERR_INVALID_ARG, "plan or output is NULL");
     if (n < P->S) return fail(WDD_ERR_INVALID_ARG, "output shorter than the scan");

@@ -163,4 +163,11 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
 cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st);
 cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st);
 
+// Reconstruction that allocates nothing (see wdd_reconstruct_noalloc): the device address of the
+// file-scope scratch array for `device` (resolved on first use), its size, and the launcher.
+cudaError_t noalloc_scratch(int device, void** out);
+size_t noalloc_scratch_limit();
+cudaError_t launch_reconstruct_noalloc(void* scratch, const float2* W, const float2* H, int Sy,
+                                       int Sx, int K, float2* obj, float* phase, cudaStream_t st);
+
 }  // namespace wdd

@@ -5,6 +5,8 @@
 // The deconvolution reads H and W once (HBM bound); the inverse DFT runs
 // row-column on the S_y x S_x spectrum with exact integer twiddle indices.
 
+#include <mutex>
+
 #include "wdd_internal.h"
 
 namespace wdd {
@@ -123,6 +125,69 @@ cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st) {
     int warps_per_block = kThreads / 32;
     int blocks = (P->S + warps_per_block - 1) / warps_per_block;
     deconvolve_kernel<<<blocks, kThreads, 0, st>>>(P->d_W, P->d_H, P->d_o, P->S, P->K);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Twiddles exp(+2 pi i m / n) for both scan axes (the same expression as the plan's tables).
+__global__ void idft_tables_kernel(float2* twy, int Sy, float2* twx, int Sx) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < Sy) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)Sy, &s, &c);
+        twy[t] = make_float2((float)c, (float)s);
+    }
+    if (t < Sx) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)Sx, &s, &c);
+        twx[t] = make_float2((float)c, (float)s);
+    }
+}
+
+// ---- reconstruction without allocation ---------------------------------------------------
+// Scratch for wdd_reconstruct_noalloc: spectrum (S), inverse-DFT intermediate (S) and the two
+// twiddle tables, in one file-scope device array that every call shares.  Each call writes all
+// of the scratch it reads, so nothing needs clearing between calls.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices];   // device address of the scratch, per device
+static std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+cudaError_t noalloc_scratch(int device, void** out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        // the host-side symbol is only a stand-in: the kernel needs the device address
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = prepare_reconstruct_kernels();
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+size_t noalloc_scratch_limit() { return kNoAllocScratchBytes; }
+
+cudaError_t launch_reconstruct_noalloc(void* scratch, const float2* W, const float2* H, int Sy,
+                                       int Sx, int K, float2* obj, float* phase, cudaStream_t st) {
+    const int S = Sy * Sx;
+    float2* o = static_cast<float2*>(scratch);
+    float2* X = o + S;
+    float2* twy = X + S;
+    float2* twx = twy + Sy;
+    const int nt = Sy > Sx ? Sy : Sx;
+    idft_tables_kernel<<<(nt + kThreads - 1) / kThreads, kThreads, 0, st>>>(twy, Sy, twx, Sx);
+    deconvolve_kernel<<<(S + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(W, H, o, S, K);
+    idft_rows_kernel<<<Sy, kThreads, 2 * sizeof(float2) * Sx, st>>>(o, twx, X, Sy, Sx);
+    idft_cols_kernel<<<Sx, kThreads, 2 * sizeof(float2) * Sy, st>>>(X, twy, obj, phase, Sy, Sx);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,9 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_get_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "wdd_check_device": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64]),
+    "wdd_reconstruct_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
     "wdd_get_hit_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wdd_copy_array": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -315,3 +318,18 @@ class Plan:
 def selftest_bounded_wait(wait_ns: int = 50_000_000) -> int:
     """Runs the device bounded-wait self test; returns the status code (ERR_TIMEOUT expected)."""
     return int(lib().wdd_selftest_bounded_wait(int(wait_ns)))
+
+
+def reconstruct_noalloc(weights, accum, scan_y: int, scan_x: int, rank_k: int, obj, phase=None,
+                        stream=None) -> None:
+    """Reconstruction that allocates no device memory (wdd_reconstruct_noalloc): for callers
+    that cannot allocate, such as code running during CUDA graph capture.  All buffers are the
+    caller's device tensors; the library's fixed scratch holds the intermediates."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().wdd_reconstruct_noalloc(ctypes.c_void_p(_ptr(weights)), ctypes.c_void_p(_ptr(accum)),
+                                         scan_y, scan_x, rank_k, ctypes.c_void_p(_ptr(obj)),
+                                         ctypes.c_void_p(_ptr(phase)) if phase is not None else None,
+                                         ctypes.c_void_p(int(stream.cuda_stream))),
+           "wdd_reconstruct_noalloc")
