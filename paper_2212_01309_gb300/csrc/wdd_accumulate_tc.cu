@@ -215,8 +215,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 if (acc >= (uint32_t)a.lcm) acc -= (uint32_t)a.lcm;
             }
         }
+        // first and last frame index of this thread's K-step, prefetched one stage ahead
+        int32_t nf = __ldg(a.idx + kstep * 16), nl = __ldg(a.idx + kstep * 16 + 15);
         for (int it = 0; it < a.stages_total; ++it) {
             const int st = it % SE;
+            const int32_t s_first = nf, s_last = nl;
+            if (it + 1 < a.stages_total) {
+                nf = __ldg(a.idx + (it + 1) * kChunk + kstep * 16);
+                nl = __ldg(a.idx + (it + 1) * kChunk + kstep * 16 + 15);
+            }
             // one lane per warp waits for the stage to be free and tells its warp
             int ok = 1;
             if (lane == 0) {
@@ -233,7 +240,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             // consecutive positions of one scan row, so m advances by dx = vx mx per frame.
             // Otherwise each frame's index is decoded on its own.
             const int32_t* ip = a.idx + it * kChunk + kstep * 16;
-            const int32_t s_first = __ldg(ip), s_last = __ldg(ip + 15);
             uint32_t mm[16];
             {
                 const uint32_t s0 = (uint32_t)s_first;
