@@ -7,10 +7,10 @@
  *   plan    (Algorithm 1)  reduced detector basis P, probe autocorrelation Y_v for every scan
  *                          frequency v, chi_v = P vec(Y_v), Wiener filter
  *                          W_v = conj(chi_v) / (|chi_v|^2 + eps_eff), active-frequency mask
- *                          (Sect. 6.3).  Built once, in FP64 on the GPU.
- *   push    (Algorithm 2)  per frame: c_s = P vec(I_s) (Sect. 5, operator H), then
+ *                          (Sect. 6.2, Eq. 15).  Built once, in FP64 on the GPU.
+ *   push    (Algorithm 2)  per frame: c_s = P vec(I_s) (Sect. 5, operator H of Eq. 12), then
  *                          H[v,k] += exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x)) c_s[k]
- *                          (Eq. outer_prod: partial sums of F_2D I over the frames at hand).
+ *                          (Eq. 14: partial sums of F_2D I over the frames at hand).
  *   snapshot / finalize    o_v = sum_k W_v[k] H[v,k]  (Hadamard product with K_v and sum of all
  *                          elements, Algorithm 2), o <- o / sqrt(o_0) (Eq. 3), and
  *                          O = conj(IFFT2(o)) (Algorithm 2, last step), at any time in the scan.
@@ -48,7 +48,7 @@ typedef enum {
 /* Reduced detector bases.
  *  FOURIER_FULL  K = det_y * det_x real cos/sin rows of the detector inverse DFT.  Live WDD with
  *                this basis equals classical WDD (Eq. 2, Eq. 3) exactly.  det_y, det_x <= 64.
- *  HG_TENSOR     the operator H of Sect. 5: L x L Hermite-Gauss functions (Eq. 5), K = L * L.
+ *  HG_TENSOR     the operator H of Sect. 5: L x L Hermite-Gauss functions (Eq. 7), K = L * L.
  *  HG_ENERGY     the first K tensor pairs (n_y, n_x) ordered by oscillator energy n_y + n_x
  *                (Eq. 10), ties broken by smaller n_y; L is the smallest that holds them.
  * Hermite-Gauss width: sigma = R_bf / sqrt(2 (L - 1) + 1), R_bf = semiconv / (lambda * dk)
@@ -67,7 +67,7 @@ typedef enum { WDD_FRAME_U16 = 0, WDD_FRAME_F32 = 1, WDD_FRAME_F64 = 2 } wdd_fra
 
 typedef struct {
     int32_t scan_y, scan_x;   /* scan grid S_y x S_x; position s = s_y * scan_x + s_x        */
-    double scan_step_m;       /* scan step Delta in metres (equal on both axes, Sect. 6.3)     */
+    double scan_step_m;       /* scan step Delta in metres (equal on both axes, Sect. 6.2)     */
     int32_t det_y, det_x;     /* detector pixels N_y x N_x                                     */
     double det_px_inv_m;      /* detector sampling dk in reciprocal metres per pixel           */
     double voltage_v;         /* acceleration voltage (sets lambda, relativistic)              */
@@ -159,7 +159,7 @@ typedef struct {
     int32_t rank_k;          /* K                                                            */
     int32_t basis_ly;        /* basis functions along detector rows (L_y)                    */
     int32_t basis_lx;        /* along detector columns (L_x)                                 */
-    int32_t n_active;        /* active scan frequencies (Sect. 6.3 overlap criterion)        */
+    int32_t n_active;        /* active scan frequencies (Sect. 6.2 overlap criterion)        */
     double eps_eff;          /* epsilon actually added to |chi|^2                            */
     double wavelength_m;     /* lambda                                                       */
     double bf_radius_px;     /* bright-field radius R_bf in detector pixels                  */

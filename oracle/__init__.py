@@ -8,9 +8,12 @@ helpers with the CUDA library.
 Modules
   wdd_oracle  classical WDD (Eq. 2, Eq. 3), the pre-computed Wiener filter (Algorithm 1), the
               modified live WDD (Algorithm 2), the Hermite-Gauss bases (Sect. 4, Sect. 5) and the
-              overlap criterion (Sect. 6.3).
+              overlap criterion (Sect. 6.2, Eq. 15-17).
 
-Parity status of each function is given in its docstring; functions whose result has no
-independent pin say "parity unpinned".
+Pins: tests/test_oracle_pins.py checks every function against values the paper prints, closed
+forms, library routines, brute force and exact invariants, and tests/test_oracle_mutations.py
+plants plausible mistakes and checks that the pins catch them.  One quantity has no independent
+pin: the absolute amplitude scale of the reconstructed object (the division by sqrt(o_0) in
+``finalize``), so its parity is unpinned; only the phase is graded.
 """
 from .wdd_oracle import *  # noqa: F401,F403

@@ -52,14 +52,14 @@ SPEED_OF_LIGHT = 299792458.0
 
 
 # ---------------------------------------------------------------------------------------------
-# Acquisition geometry (Sect. 6.3, Eq. 12-14)
+# Acquisition geometry (Sect. 6.2, Eq. 15-17)
 # ---------------------------------------------------------------------------------------------
 
 def electron_wavelength(voltage_v: float) -> float:
     """Relativistic de Broglie wavelength lambda(V) in metres.
 
     lambda = h / sqrt(2 m0 e V (1 + e V / (2 m0 c^2))).  Evaluated as a fixed sequence of
-    correctly rounded IEEE operations.  Pinned by the 200 kV value 2.508 pm quoted in Sect. 6.3.
+    correctly rounded IEEE operations.  Pinned by the 200 kV value 2.508 pm quoted in Sect. 6.2.
     """
     ev = ELEMENTARY_CHARGE * voltage_v
     rel = 1.0 + ev / (2.0 * ELECTRON_MASS * SPEED_OF_LIGHT * SPEED_OF_LIGHT)
@@ -67,7 +67,7 @@ def electron_wavelength(voltage_v: float) -> float:
 
 
 def overlap_bound_ratio(step_m: float, semiconv_rad: float, wavelength_m: float) -> float:
-    """S_hat / S = sqrt(2) * Delta * sin(theta) / lambda (Eq. 14).  Pinned by the 0.47 example."""
+    """S_hat / S = sqrt(2) * Delta * sin(theta) / lambda (Eq. 17).  Pinned by the 0.47 example."""
     return math.sqrt(2.0) * step_m * math.sin(semiconv_rad) / wavelength_m
 
 
@@ -121,7 +121,7 @@ def signed_freq(v: np.ndarray | int, n: int):
 
 
 def scan_shift_px(p: Params) -> tuple[np.ndarray, np.ndarray]:
-    """Detector-pixel shift q_v / dk of every scan frequency, per axis (Eq. 13 geometry).
+    """Detector-pixel shift q_v / dk of every scan frequency, per axis (Eq. 16 geometry).
 
     q_v = (f_y / (S_y * Delta), f_x / (S_x * Delta)) in reciprocal metres with signed
     frequencies f; dividing by the detector sampling dk gives pixels.
@@ -139,7 +139,7 @@ def bright_field_radius_px(p: Params) -> float:
 
 
 def active_mask(p: Params) -> np.ndarray:
-    """Frequencies whose shifted aperture discs intersect: |q_v| < 2 R (reading R8, Eq. 12)."""
+    """Frequencies whose shifted aperture discs intersect: |q_v| < 2 R (reading R8, Eq. 15)."""
     qy, qx = scan_shift_px(p)
     r = bright_field_radius_px(p)
     d2 = qy[:, None] * qy[:, None] + qx[None, :] * qx[None, :]
@@ -181,12 +181,12 @@ def probe_autocorrelation(p: Params, vy: int, vx: int) -> np.ndarray:
 # ---------------------------------------------------------------------------------------------
 
 def hg_functions_1d(n_pts: int, L: int, sigma: float, center: float) -> np.ndarray:
-    """Sampled 1-D oscillator eigenfunctions psi_0..psi_{L-1} (Eq. 5), shape (n_pts, L).
+    """Sampled 1-D oscillator eigenfunctions psi_0..psi_{L-1} (Eq. 7), shape (n_pts, L).
 
     psi_n(x) is proportional to H_n(x / sigma) exp(-x^2 / (2 sigma^2)); the normalised three-term
     recurrence avoids overflowing H_n.  Each column is then scaled to unit discrete L2 norm
     (reading R4).  Pinned against numpy's Hermite polynomial evaluation and the oscillator
-    eigen-energies of Eq. 4.
+    eigen-energies of Eq. 6.
     """
     x = (np.arange(n_pts, dtype=np.float64) - center) / sigma
     out = np.zeros((n_pts, L), dtype=np.float64)
@@ -241,7 +241,7 @@ class OraclePlan:
 
 
 def project_operator(A: np.ndarray, By: np.ndarray, Bx: np.ndarray) -> np.ndarray:
-    """The reduction operator H of Sect. 5 on one detector image: Z = By^T A Bx.
+    """The reduction operator H of Sect. 5 (Eq. 12) on one detector image: Z = By^T A Bx.
 
     Z[ly, lx] = sum_{i,j} By[i, ly] A[i, j] Bx[j, lx].  (Sect. 5 writes psi_x^T A^T psi_y, the
     transpose of the same matrix; data and probe pass through the same map, so the orientation
@@ -346,7 +346,7 @@ def fourier_window_plan(p: Params, keep_k: int) -> OraclePlan:
 
 
 # ---------------------------------------------------------------------------------------------
-# Streaming path (Algorithm 2, Eq. outer_prod)
+# Streaming path (Algorithm 2, Eq. 14)
 # ---------------------------------------------------------------------------------------------
 
 def coefficients(frames: np.ndarray, plan: OraclePlan) -> np.ndarray:
@@ -373,7 +373,7 @@ def phase_factor(p: Params, v: np.ndarray, s: np.ndarray) -> np.ndarray:
 
 def accumulate(C: np.ndarray, scan_idx: np.ndarray, p: Params,
                v_rows: np.ndarray | None = None, chunk: int = 2048) -> np.ndarray:
-    """H[v, k] = sum_s F_2D[v, s] c_s[k]: Eq. outer_prod as one matrix product per row block.
+    """H[v, k] = sum_s F_2D[v, s] c_s[k]: Eq. 14 as one matrix product per row block.
 
     Returns H for the requested rows (all S by default), complex (len(v_rows), K).
     """
@@ -396,7 +396,9 @@ def deconvolve(H: np.ndarray, plan: OraclePlan, v_rows: np.ndarray | None = None
 def finalize(o: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
     """Eq. 3 normalisation by sqrt(o_0), then conj(F^-1(O)) of Algorithm 2 (reading R6).
 
-    Returns (complex object transfer function S_y x S_x, phase in radians).
+    Returns (complex object transfer function S_y x S_x, phase in radians).  The phase is pinned
+    (weak-phase recovery, roll and conjugation invariants); the absolute amplitude scale is
+    parity unpinned.
     """
     o = np.asarray(o, dtype=np.complex128).reshape(p.scan_y, p.scan_x)
     o0 = o[0, 0]

@@ -1,6 +1,6 @@
 // Phase accumulation on the SIMT cores in FP32 (the plain path):
 //   H[v, k] += sum_b E[v, s_b] c_b[k],   E[v, s] = exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x))
-// which is Eq. outer_prod restricted to the frames at hand (Algorithm 2: the subset of F_2D for
+// which is Eq. 14 restricted to the frames at hand (Algorithm 2: the subset of F_2D for
 // each s built from the two 1-D DFT matrices).  The phase factor is never read from HBM: its
 // exact integer index m = (v_y s_y mod S_y) * (lcm / S_y) + (v_x s_x mod S_x) * (lcm / S_x)
 // (mod lcm) selects an entry of an lcm-long table of exp(-2 pi i m / lcm) built in FP64.

@@ -1,5 +1,5 @@
 // Phase accumulation on the 5th-generation tensor cores (tcgen05, TMEM), split FP16 precision:
-//   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. outer_prod, Algorithm 2)
+//   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. 14, Algorithm 2)
 //
 // Computed transposed, D^T = C^T E^T, so that every UMMA is as wide as the hardware allows:
 //   A operand (M = 128 rows): 64 coefficients, rows 0-63 their FP16 hi parts and rows 64-127 their

@@ -1,5 +1,5 @@
 // Host side of the C ABI declared in include/wdd.h: parameter validation, the plan-time
-// geometry of Sect. 6.3, exact scan bookkeeping, staging of projected frames and the order of
+// geometry of Sect. 6.2, exact scan bookkeeping, staging of projected frames and the order of
 // kernel launches for Algorithm 1 (plan), Algorithm 2 (push) and Eq. 3 (snapshot).
 //
 // Host floating point that decides an integer (aperture radius, frequency shifts, the
@@ -319,7 +319,7 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     P->lcm = std::lcm(P->Sy, P->Sx);
     cudaGetDevice(&P->device);
 
-    // ---- geometry (Sect. 6.3) ------------------------------------------------------------
+    // ---- geometry (Sect. 6.2) ------------------------------------------------------------
     P->lambda = electron_wavelength(p.voltage_v);
     P->R = p.semiconv_rad / (P->lambda * p.det_px_inv_m);
 
@@ -395,7 +395,7 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
         return fail(WDD_ERR_UNSUPPORTED, "rank above 4096");
     }
 
-    // ---- shifts and active mask (Sect. 6.3; R8: |q_v| < 2 R strictly) ----------------------
+    // ---- shifts and active mask (Sect. 6.2, Eq. 15; R8: |q_v| < 2 R strictly) ----------------------
     std::vector<double> qy(P->Sy), qx(P->Sx);
     {
         double den_y = ((double)P->Sy * p.scan_step_m) * p.det_px_inv_m;

@@ -21,7 +21,7 @@ __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {  // a * con
     return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Normalised 1-D oscillator eigenfunctions (Eq. 5) by the three-term recurrence:
+// Normalised 1-D oscillator eigenfunctions (Eq. 7) by the three-term recurrence:
 //   psi_0 = pi^-1/4 exp(-x^2/2), psi_1 = sqrt(2) x psi_0,
 //   psi_{n+1} = sqrt(2/(n+1)) x psi_n - sqrt(n/(n+1)) psi_{n-1},  x = (j - center) / sigma.
 // One thread per sample; column norms are fixed by hg_normalise_kernel.

@@ -1,4 +1,4 @@
-// Frame ingest and projection onto the reduced basis (Sect. 5 operator H; Algorithm 2, step 1):
+// Frame ingest and projection onto the reduced basis (Sect. 5, operator H of Eq. 12; Algorithm 2, step 1):
 //   c_b[k] = component_k( sum_{i,j} By[i, ly_k] I_b[i, j] Bx[j, lx_k] )
 // computed separably: U = By^T I (contraction over detector rows), then Z = U Bx.
 //

@@ -1,7 +1,7 @@
 """Seeded synthetic 4D-STEM inputs shared by the tests, the benchmark and the oracle checks.
 
 This package simulates acquisitions (the forward model of Eq. 1 with the Poisson dose model of
-Sect. 7) and nothing else: it holds none of the reconstruction arithmetic, so that the CUDA path
+Sect. 8) and nothing else: it holds none of the reconstruction arithmetic, so that the CUDA path
 and the CPU oracle can both consume its arrays without sharing any of the method's code.
 """
 from .generator import (  # noqa: F401

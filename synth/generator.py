@@ -4,7 +4,7 @@ Forward model (Eq. 1): for scan position s the detector records
     I_s = |fftshift(FFT2(p(r - r_s) * O(r)))|^2
 on an N x N window of object pixels, with O = exp(i*phi) a periodic weak phase object and p the
 probe formed by a hard-edged circular aperture with defocus.  Optional Poisson noise follows the
-dose model of Sect. 7 (counts ~ Poisson(dose * I_s / sum(I_s))), with the dose given per frame.
+dose model of Sect. 8 (counts ~ Poisson(dose * I_s / sum(I_s))), with the dose given per frame.
 
 Choices the paper leaves open (they are restated in the design notes):
   * object pixel dx = lambda / (4 * theta), so the bright-field disc radius is N/4 detector pixels

@@ -71,7 +71,7 @@ def test_overlap_bound_matches_paper_example():
 
 
 def test_hg_matches_hermite_polynomials():
-    """Recurrence-built columns equal H_n(x/sigma) exp(-x^2/2sigma^2), normalised (Eq. 5)."""
+    """Recurrence-built columns equal H_n(x/sigma) exp(-x^2/2sigma^2), normalised (Eq. 7)."""
     from numpy.polynomial import hermite as Hm
     for n_pts, L, sigma, c in [(64, 10, 5.3, 32.0), (97, 7, 9.1, 40.5), (33, 16, 3.0, 16.0)]:
         got = W.hg_functions_1d(n_pts, L, sigma, c)
@@ -90,7 +90,7 @@ def test_hg_orthonormal_when_well_sampled():
 
 
 def test_hg_eigen_energies():
-    """Rayleigh quotient of H = -d2/2 + x^2/(2 sigma^4) on psi_n gives sigma^-2 (n + 1/2) (Eq. 4)."""
+    """Rayleigh quotient of H = -d2/2 + x^2/(2 sigma^4) on psi_n gives sigma^-2 (n + 1/2) (Eq. 6)."""
     off = _golden()["hg_eigen_energy"]["offset_1d"]
     sigma, npts = 50.0, 1200
     B = W.hg_functions_1d(npts, 8, sigma, npts / 2)
@@ -115,7 +115,7 @@ def test_hg_2d_energy_ordering():
 
 
 def test_fourier_eigen_property():
-    """Sampled psi_n with sigma^2 = N / (2 pi) is a DFT eigenvector with eigenvalue (-i)^n (Eq. 6)."""
+    """Sampled psi_n with sigma^2 = N / (2 pi) is a DFT eigenvector with eigenvalue (-i)^n (Eq. 11)."""
     N = 256
     sigma = math.sqrt(N / (2 * math.pi))
     B = W.hg_functions_1d(N, 9, sigma, N / 2)
@@ -160,7 +160,7 @@ def test_projection_operator_brute_force():
 
 
 def test_incremental_phase_sum_is_scan_dft():
-    """sum_s F_2D[v, s] c_s (Eq. outer_prod) equals numpy's 2-D FFT over the scan axes."""
+    """sum_s F_2D[v, s] c_s (Eq. 14) equals numpy's 2-D FFT over the scan axes."""
     p = W.Params(scan_y=6, scan_x=10, scan_step_m=1e-10, det_y=4, det_x=4, det_px_inv_m=1e9,
                  voltage_v=3e5, semiconv_rad=0.02, defocus_m=0, epsilon=1e-3, rank_k=4)
     rng = np.random.default_rng(1)
@@ -296,7 +296,7 @@ def test_invariant_vacuum():
 
 
 def test_invariant_order_and_partition_merge():
-    """Frame order does not matter and partial results merge by summation (Sect. 6.4, Fig. 17)."""
+    """Frame order does not matter and partial results merge by summation (Sect. 6.3 and the live-update figure of Sect. 9)."""
     acq, _ = synth.config("c1")
     F = synth.all_frames(acq)
     idx = synth.raster_indices(acq)
@@ -310,7 +310,7 @@ def test_invariant_order_and_partition_merge():
     assert W.complex_rel_l2(merged, full) < 1e-12
 
 
-# ---- overlap criterion (Sect. 6.3) -----------------------------------------------------------
+# ---- overlap criterion (Sect. 6.2) -----------------------------------------------------------
 
 def test_active_mask_matches_disc_geometry():
     acq, _ = synth.config("c1")
@@ -333,14 +333,14 @@ def test_active_mask_matches_disc_geometry():
             near_edge = abs(math.hypot(qy[vy], qx[vx]) - 2 * R) < 0.02 * R
             if not near_edge:
                 assert overlap == bool(mask[vy, vx]), (vy, vx)
-    # Eq. 14 is sufficient: every frequency within the square bound S_hat is active
+    # Eq. 17 is sufficient: every frequency within the square bound S_hat is active
     fy = W.signed_freq(np.arange(16), 16)
     fx = W.signed_freq(np.arange(12), 12)
     for vy in range(16):
         for vx in range(12):
             shat_y = W.overlap_bound_ratio(p.scan_step_m, p.semiconv_rad, p.wavelength_m) * 16
             shat_x = W.overlap_bound_ratio(p.scan_step_m, p.semiconv_rad, p.wavelength_m) * 12
-            # Eq. 14 as printed uses one S for both axes; it is applied per axis here
+            # Eq. 17 as printed uses one S for both axes; it is applied per axis here
             if max(abs(fy[vy]) / shat_y, abs(fx[vx]) / shat_x) <= 1 - 1e-9:
                 assert mask[vy, vx]
 
