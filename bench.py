@@ -183,6 +183,51 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------------
+# serving mode: six concurrent sessions, seeded Poisson arrivals at 20k frames/s
+# ---------------------------------------------------------------------------------------------
+
+def run_serving(args) -> int:
+    import torch
+
+    import synth
+    from paper_2212_01309_gb300 import serving, wdd
+    from synth.torch_gen import TorchFrames
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    mix = synth.serving_mix()
+    sessions = []
+    for sid, (acq, rc) in enumerate(mix):
+        frames = TorchFrames(acq).all()
+        p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                        epsilon=rc["epsilon"], precision="split", max_batch=512,
+                                        accum_depth=2048, overlap_pushes=True)
+        sessions.append(serving.Session(sid=sid, params=p, frames=frames, n_frames=acq.n_frames))
+    torch.cuda.synchronize()
+    arrivals = synth.serving_arrivals([s.n_frames for s in sessions])
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.5, 64 << 30))
+    out = {"mode": "serving", "metric": METRIC, "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "6 sessions: scan/detector 64^2/64^2, 128^2/64^2, 128^2/128^2, "
+                                  "256^2/128^2, 192x256/96^2, 256^2/256^2; uint16 Poisson frames; "
+                                  "batches of 16-512 frames; snapshot every 1024 frames per session",
+                      "arrival_rate_fps": 20000, "frames": sum(s.n_frames for s in sessions),
+                      "schedule_s": arrivals[-1][0], "hbm_budget_bytes": budget,
+                      "precision": "split", "cuda_graph_snapshots": True}}
+    for mode in ("open_loop", "closed_loop"):
+        srv = serving.Server(hbm_budget_bytes=budget, snapshot_every=1024, use_graphs=True)
+        for s in sessions:
+            srv.add_session(s)
+        setup = srv.admit_now()          # plans (Algorithm 1) built when the sessions are set up
+        torch.cuda.synchronize()
+        st = srv.run(arrivals, open_loop=(mode == "open_loop"), timeout_s=1800)
+        st["session_setup_s"] = setup
+        out[mode] = st
+    out["value"] = out["closed_loop"]["frames_per_s"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
 
@@ -194,10 +239,14 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["auto", "fp32", "split"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the multi-session serving workload instead (separate JSON line)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist

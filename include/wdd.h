@@ -110,6 +110,11 @@ typedef struct wdd_plan wdd_plan;
  * OUT_OF_MEMORY, CUDA. */
 wdd_status wdd_plan_create(const wdd_params* p, wdd_plan** out);
 
+/* Validates *p exactly as wdd_plan_create does and reports in *bytes the device memory such a
+ * plan would hold, without touching the GPU (admission control by memory budget).  Returns the
+ * status wdd_plan_create would return for these parameters (memory-independent errors only). */
+wdd_status wdd_plan_footprint(const wdd_params* p, int64_t* bytes);
+
 /* Releases every device and host buffer of the plan (synchronises with its last stream). */
 wdd_status wdd_plan_destroy(wdd_plan* plan);
 
@@ -144,6 +149,11 @@ wdd_status wdd_snapshot(wdd_plan* plan, wdd_result* out);
 /* As wdd_snapshot, then marks the plan finished: later pushes return WDD_ERR_STATE.  An
  * incomplete scan is not an error; positions_covered reports the coverage. */
 wdd_status wdd_finalize(wdd_plan* plan, wdd_result* out);
+
+/* Accumulates the frames staged so far (Algorithm 2 loop body for them) on the plan's stream.
+ * After it, a snapshot enqueues only the deconvolution and the inverse DFT, a fixed sequence of
+ * launches that can be captured once in a CUDA graph and replayed. */
+wdd_status wdd_flush(wdd_plan* plan);
 
 /* Sets the stream on which the plan's next snapshot, finalize or reset is enqueued (pushes set
  * it too).  Work already enqueued on the previous stream is ordered before later work on the

@@ -269,7 +269,10 @@ wdd_status wdd_params_default(wdd_params* p) {
     return WDD_OK;
 }
 
-wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
+namespace {
+// Creates a plan, or (footprint != NULL) only validates the parameters and reports the device
+// bytes the plan would hold, without touching the GPU.
+wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* footprint) {
     if (!prm || !out) return fail(WDD_ERR_INVALID_ARG, "params or out is NULL");
     *out = nullptr;
     const wdd_params& p = *prm;
@@ -317,7 +320,7 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
         return fail(WDD_ERR_INVALID_ARG, "split precision stages at most 8192 frames");
     }
     P->lcm = std::lcm(P->Sy, P->Sx);
-    cudaGetDevice(&P->device);
+    if (!footprint) cudaGetDevice(&P->device);
 
     // ---- geometry (Sect. 6.2) ------------------------------------------------------------
     P->lambda = electron_wavelength(p.voltage_v);
@@ -419,6 +422,11 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
 
     // ---- memory budget -----------------------------------------------------------------
     int64_t need = planned_bytes(P);
+    if (footprint) {
+        *footprint = need;
+        delete P;
+        return WDD_OK;
+    }
     if (p.hbm_budget_bytes > 0 && need > p.hbm_budget_bytes) {
         delete P;
         char buf[160];
@@ -540,10 +548,26 @@ wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
     return WDD_OK;
 }
 
+}  // namespace
+
+wdd_status wdd_plan_create(const wdd_params* prm, wdd_plan** out) {
+    return plan_create_impl(prm, out, nullptr);
+}
+
+wdd_status wdd_plan_footprint(const wdd_params* prm, int64_t* bytes) {
+    if (!bytes) return fail(WDD_ERR_INVALID_ARG, "bytes is NULL");
+    wdd_plan* unused = nullptr;
+    return plan_create_impl(prm, &unused, bytes);
+}
+
+wdd_status wdd_flush(wdd_plan* P) {
+    if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
+    return flush(P);
+}
+
 wdd_status wdd_plan_destroy(wdd_plan* P) {
     if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
     if (P->stream) cudaStreamSynchronize(P->stream);
-    cudaDeviceSynchronize();
     release(P);
     delete P;
     return WDD_OK;

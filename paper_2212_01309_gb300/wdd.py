@@ -83,6 +83,8 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
     "wdd_plan_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
     "wdd_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "wdd_plan_footprint": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64)]),
+    "wdd_flush": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_push_frames": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int64, ctypes.c_void_p]),
     "wdd_snapshot": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Result)]),
@@ -168,6 +170,13 @@ def params_from_acquisition(acq, *, basis, rank_k, epsilon=1e-3, **kw) -> Params
                        frame_dtype=acq.dtype, **kw)
 
 
+def plan_footprint(params: Params) -> int:
+    """Device bytes a plan with these parameters would hold (no GPU work)."""
+    b = ctypes.c_int64()
+    _check(lib().wdd_plan_footprint(ctypes.byref(params), ctypes.byref(b)), "wdd_plan_footprint")
+    return int(b.value)
+
+
 def _ptr(x) -> int:
     """Address of a torch tensor or numpy array's data (no copy)."""
     if hasattr(x, "data_ptr"):
@@ -250,6 +259,12 @@ class Plan:
         if stream is not None:
             self.set_stream(stream)
         return self._result(lib().wdd_finalize, obj, phase)
+
+    def flush(self, stream=None) -> None:
+        """Accumulates the staged frames now (a later snapshot then only reconstructs)."""
+        if stream is not None:
+            self.set_stream(stream)
+        _check(lib().wdd_flush(self._h), "wdd_flush")
 
     def set_stream(self, stream) -> None:
         _check(lib().wdd_set_stream(self._h, ctypes.c_void_p(int(stream.cuda_stream))),

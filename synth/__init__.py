@@ -15,4 +15,7 @@ from .generator import (  # noqa: F401
     frames,
     all_frames,
     raster_indices,
+    serving_mix,
+    serving_arrivals,
+    SERVING_SIZES,
 )

@@ -263,3 +263,55 @@ def all_frames(acq: Acquisition, obj: np.ndarray | None = None) -> np.ndarray:
     for idx, fr in frames(acq, 0, acq.n_frames, chunk=1024, obj=obj):
         out[idx] = fr
     return out
+
+
+# ---- serving mix: several concurrent acquisitions and their frame arrivals -----------------
+
+SERVING_SIZES = [((64, 64), 64), ((128, 128), 64), ((128, 128), 128), ((256, 256), 128),
+                 ((192, 256), 96), ((256, 256), 256)]
+
+
+def serving_mix(seed_obj: int = 1004, seed_noise: int = 2004, sizes=None, scale: int = 1):
+    """Sessions of the serving workload: (scan, detector) sizes as listed, uint16 Poisson frames,
+    dose log-uniform in [1e2, 1e4] per frame, semiconvergence U[15, 30] mrad, defocus
+    U[-10, 10] nm, 300 kV, object twice the scan (scan step 2 px).  K = 64 for detectors up to 96
+    pixels, 128 for 128, 256 for 256 (Hermite-Gauss energy basis for 128, tensor otherwise).
+    `scale` divides every scan side (smaller copies of the mix for tests).
+    Returns a list of (Acquisition, recon dict)."""
+    rng = np.random.default_rng(seed_obj)
+    out = []
+    for i, ((sy, sx), n) in enumerate(sizes or SERVING_SIZES):
+        sy, sx = max(4, sy // scale), max(4, sx // scale)
+        dose = float(10 ** rng.uniform(2.0, 4.0))
+        theta = float(rng.uniform(15e-3, 30e-3))
+        df = float(rng.uniform(-10e-9, 10e-9))
+        acq = Acquisition(scan_y=sy, scan_x=sx, det=n, obj_y=2 * sy, obj_x=2 * sx,
+                          n_atoms=max(8, (sy * sx) // 40), peak_phase=0.2, voltage_v=300e3,
+                          semiconv_rad=theta, defocus_m=df, dose=dose, dtype="u16",
+                          seed_obj=seed_obj * 10 + i, seed_noise=seed_noise * 10 + i)
+        k = 64 if n <= 96 else (128 if n == 128 else 256)
+        basis = "hg_energy" if k == 128 else "hg_tensor"
+        out.append((acq, dict(basis=basis, rank_k=k, epsilon=1e-3)))
+    return out
+
+
+def serving_arrivals(n_frames, rate_fps: float = 20000.0, seed: int = 3004,
+                     bmin: int = 16, bmax: int = 512):
+    """Seeded Poisson-process arrivals: batches of b ~ U{bmin..bmax} frames at exponential gaps
+    with mean b / rate; each batch goes to a session drawn in proportion to its remaining frames
+    and continues that session's raster order.  Returns a list of (t_seconds, session, start,
+    count)."""
+    rng = np.random.default_rng(seed)
+    left = np.array(n_frames, dtype=np.int64)
+    nxt = np.zeros(len(n_frames), dtype=np.int64)
+    t = 0.0
+    out = []
+    while left.sum() > 0:
+        b = int(rng.integers(bmin, bmax + 1))
+        t += float(rng.exponential(b / rate_fps))
+        sid = int(rng.choice(len(left), p=left / left.sum()))
+        c = int(min(b, left[sid]))
+        out.append((t, sid, int(nxt[sid]), c))
+        nxt[sid] += c
+        left[sid] -= c
+    return out

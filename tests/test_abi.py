@@ -92,3 +92,20 @@ def test_invalid_params_rejected_on_host(wdd):
     assert L.wdd_push_frames(None, None, None, 0, None) == wdd.ERR_INVALID_ARG
     assert L.wdd_snapshot(None, None) == wdd.ERR_INVALID_ARG
     assert L.wdd_plan_destroy(None) == wdd.ERR_INVALID_ARG
+
+
+def test_plan_footprint_without_gpu(wdd):
+    """The footprint call validates like plan creation and sizes the plan without a GPU."""
+    small = wdd.make_params(scan_y=32, scan_x=32, scan_step_m=1e-10, det_y=32, det_x=32,
+                            det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=64)
+    big = wdd.make_params(scan_y=256, scan_x=256, scan_step_m=1e-10, det_y=128, det_x=128,
+                          det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=256,
+                          precision="split", accum_depth=4096)
+    a, b = wdd.plan_footprint(small), wdd.plan_footprint(big)
+    assert 0 < a < b
+    # W and H alone: 2 x S x K x 8 bytes
+    assert b >= 2 * 65536 * 256 * 8
+    bad = wdd.make_params(scan_y=32, scan_x=32, scan_step_m=1e-10, det_y=32, det_x=32,
+                          det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=63)
+    with pytest.raises(wdd.WddError):
+        wdd.plan_footprint(bad)

@@ -1,0 +1,93 @@
+"""Multi-session serving (paper_2212_01309_gb300.serving) on the GPU.
+
+Each session's reconstruction must be the same whether it runs alone or in the mix, whether the
+HBM budget forces sessions to queue, and whether snapshots replay captured CUDA graphs; the
+smallest session is also checked against the FP64 oracle.  Tolerance: the FP32 path's phase
+bound (1e-5 relative L2); in practice the results are bit-identical, because a session's frames
+are projected one by one and flushed only at its own snapshot points.
+"""
+import numpy as np
+import pytest
+
+import oracle.wdd_oracle as W
+import synth
+from wdd_harness import phase_err
+
+pytestmark = pytest.mark.gpu
+
+PHASE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mix():
+    import torch
+    from paper_2212_01309_gb300 import serving, wdd
+    from synth.torch_gen import TorchFrames
+    assert torch.cuda.is_available()
+    sessions = []
+    for sid, (acq, rc) in enumerate(synth.serving_mix(scale=8)):
+        frames = TorchFrames(acq).all()
+        p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                        epsilon=rc["epsilon"], max_batch=512, accum_depth=2048)
+        sessions.append((acq, rc, serving.Session(sid=sid, params=p, frames=frames,
+                                                  n_frames=acq.n_frames)))
+    arrivals = synth.serving_arrivals([a.n_frames for a, _, _ in sessions], seed=77)
+    return sessions, arrivals
+
+
+def _serve(sessions, arrivals, budget=None, graphs=True, snapshot_every=256):
+    from paper_2212_01309_gb300 import serving
+    srv = serving.Server(hbm_budget_bytes=budget, snapshot_every=snapshot_every, use_graphs=graphs)
+    for _, _, s in sessions:
+        srv.add_session(s)
+    stats = srv.run(arrivals, open_loop=False, timeout_s=300)
+    return srv, stats
+
+
+def test_results_alone_equal_results_in_mix(mix):
+    sessions, arrivals = mix
+    srv, stats = _serve(sessions, arrivals)
+    assert stats["sessions"] == len(sessions)
+    assert stats["frames"] == sum(a.n_frames for a, _, _ in sessions)
+    for sid, (acq, rc, s) in enumerate(sessions):
+        own = [(t, 0, st, c) for (t, q, st, c) in arrivals if q == sid]
+        alone, _ = _serve([(acq, rc, s)], [(t, s.sid, st, c) for (t, _, st, c) in own])
+        a = alone.results[sid].astype(np.float64)
+        b = srv.results[sid].astype(np.float64)
+        assert phase_err(b, a) <= PHASE_TOL, sid
+
+
+def test_tiny_budget_queues_sessions(mix):
+    sessions, arrivals = mix
+    from paper_2212_01309_gb300 import wdd
+    biggest = max(wdd.plan_footprint(s.params) for _, _, s in sessions)
+    ref, _ = _serve(sessions, arrivals)
+    srv, stats = _serve(sessions, arrivals, budget=biggest)
+    assert stats["sessions"] == len(sessions)
+    # never two sessions at once when any two exceed the budget: admissions interleave with ends
+    live = 0
+    peak = 0
+    for _, _, what in srv.admission_log:
+        live += 1 if what == "admit" else -1
+        peak = max(peak, live)
+    assert peak < len(sessions)
+    for sid in ref.results:
+        assert phase_err(srv.results[sid].astype(np.float64), ref.results[sid].astype(np.float64)) <= PHASE_TOL
+
+
+def test_graphs_equal_eager_snapshots(mix):
+    sessions, arrivals = mix
+    a, _ = _serve(sessions, arrivals, graphs=True)
+    b, _ = _serve(sessions, arrivals, graphs=False)
+    for sid in a.results:
+        assert np.array_equal(a.results[sid], b.results[sid])
+
+
+def test_smallest_session_matches_oracle(mix):
+    sessions, arrivals = mix
+    srv, _ = _serve(sessions, arrivals)
+    acq, rc, s = sessions[0]
+    frames = s.frames.cpu().numpy()
+    p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
+    _, ref = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
+    assert phase_err(srv.results[0].astype(np.float64), ref) <= PHASE_TOL
