@@ -112,6 +112,7 @@ struct TcArgs {
     unsigned* status;         // error word (0 = ok)
     int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_in_smem;
     int stagesE, stagesC;     // pipeline depths (E: generated phase factors, C: coefficients)
+    int rotate;               // 1: each CTA starts at its own stage (see below)
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
@@ -129,7 +130,7 @@ __host__ __device__ inline TcLayout tc_layout(int NT, int stagesE, int stagesC, 
     L.tmem = L.bar + 8 * (size_t)(2 * stagesE + 2 * stagesC + 1);
     L.scale = (L.tmem + 16 + 15) & ~size_t(15);
     L.tab = (L.scale + 4 * (size_t)NT + 15) & ~size_t(15);
-    L.total = L.tab + (tab ? 8 * (size_t)lcm : 0);
+    L.total = L.tab + (tab ? 16 * (size_t)lcm : 0);   // the table twice over: index m + d < 2 lcm
     return L;
 }
 
@@ -138,13 +139,24 @@ __device__ __forceinline__ void epilogue_barrier() {
     asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
+// 64-bit load from a shared-memory byte address.
+__device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+// kTabSmem: the phase table sits in shared memory twice over (entries m and m + lcm equal), so
+// the fast path adds a frame's phase step to a byte address with no reduction mod lcm; otherwise
+// the table is read from global memory with reduced indices.
+template <bool kTabSmem>
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NT = a.NT;                 // coefficients per CTA (64 or 128)
     const int MT = NT / 64;              // 128-row coefficient tiles (hi rows 0-63, lo rows 64-127)
     const int SE = a.stagesE, SC = a.stagesC;
-    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, a.tab_in_smem);
+    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, kTabSmem ? 1 : 0);
     const int cStageBytes = MT * 2 * kCMTileKStep;
     uint8_t* e_base = base + L.e;
     uint8_t* c_base = base + L.c;
@@ -156,13 +168,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
     float* s_scale = reinterpret_cast<float*>(base + L.scale);
     uint2* s_tab = reinterpret_cast<uint2*>(base + L.tab);
-    const uint2* tab = a.tab_in_smem ? s_tab : a.tw16;
+    const uint2* gtab = a.tw16;
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int v0 = blockIdx.x * kTileV;
     const int k0 = blockIdx.y * NT;
+    // The CTAs of a launch walk the staged frames from evenly spread starting stages, so that at
+    // any moment they read different parts of the coefficient operand instead of all fetching the
+    // same lines from L2.  Only the order of the frames' FP32 additions changes.
+    const int T = a.stages_total;
+    const int rot = a.rotate ? (int)(((long long)blockIdx.x * T) / gridDim.x) : 0;
+    auto stage_of = [T, rot](int it) { const int x = it + rot; return x >= T ? x - T : x; };
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -181,8 +199,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         int k = k0 + t;
         s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
     }
-    if (a.tab_in_smem)
-        for (int t = threadIdx.x; t < a.lcm; t += blockDim.x) s_tab[t] = a.tw16[t];
+    if (kTabSmem)
+        for (int t = threadIdx.x; t < 2 * a.lcm; t += blockDim.x)
+            s_tab[t] = a.tw16[t < a.lcm ? t : t - a.lcm];
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -198,31 +217,36 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         // ---------------- E producers: phase factors as the B operand (N rows = Re, Im) ----
         const int row = threadIdx.x & (kTileV - 1);    // 0..127
         const int kstep = threadIdx.x >> 7;            // 0..1: which 16-frame K-step of a stage
-        const int v = v0 + row;
-        const bool vok = v < a.S;
-        const uint32_t vy = vok ? (uint32_t)(v / a.Sx) : 0u;
-        const uint32_t vx = vok ? (uint32_t)(v % a.Sx) : 0u;
+        // Rows of scan frequencies beyond S (last tile) are generated for v = 0; the epilogue
+        // never writes their results.
+        const int v = (v0 + row < a.S) ? v0 + row : 0;
+        const uint32_t vy = (uint32_t)(v / a.Sx);
+        const uint32_t vx = (uint32_t)(v % a.Sx);
         const int g_re = row >> 3, g_im = 16 + (row >> 3), r = row & 7;
         // phase steps j * vx * mx mod lcm between a frame and its j-th successor in a scan row
+        // (as byte offsets into the shared table when it is there)
         uint32_t dxj[16];
         {
             const uint32_t dx = vx * (uint32_t)a.mx;   // < lcm
             uint32_t acc = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                dxj[j] = acc;
+                dxj[j] = kTabSmem ? acc * 8u : acc;
                 acc += dx;
                 if (acc >= (uint32_t)a.lcm) acc -= (uint32_t)a.lcm;
             }
         }
+        const uint32_t tab_s = smem_u32(s_tab);
         // first and last frame index of this thread's K-step, prefetched one stage ahead
-        int32_t nf = __ldg(a.idx + kstep * 16), nl = __ldg(a.idx + kstep * 16 + 15);
+        const int32_t* ip0 = a.idx + (size_t)stage_of(0) * kChunk + kstep * 16;
+        int32_t nf = __ldg(ip0), nl = __ldg(ip0 + 15);
         for (int it = 0; it < a.stages_total; ++it) {
             const int st = it % SE;
             const int32_t s_first = nf, s_last = nl;
             if (it + 1 < a.stages_total) {
-                nf = __ldg(a.idx + (it + 1) * kChunk + kstep * 16);
-                nl = __ldg(a.idx + (it + 1) * kChunk + kstep * 16 + 15);
+                const int32_t* ipn = a.idx + (size_t)stage_of(it + 1) * kChunk + kstep * 16;
+                nf = __ldg(ipn);
+                nl = __ldg(ipn + 15);
             }
             // one lane per warp waits for the stage to be free and tells its warp
             int ok = 1;
@@ -239,8 +263,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             // (mod lcm).  Fast path, decided per K-step (warp-uniform): the 16 frames are
             // consecutive positions of one scan row, so m advances by dx = vx mx per frame.
             // Otherwise each frame's index is decoded on its own.
-            const int32_t* ip = a.idx + it * kChunk + kstep * 16;
-            uint32_t mm[16];
+            const int32_t* ip = a.idx + (size_t)stage_of(it) * kChunk + kstep * 16;
+            uint32_t mm[16];   // table byte addresses (shared table) or reduced indices (global)
             {
                 const uint32_t s0 = (uint32_t)s_first;
                 const uint32_t sy0 = fastdiv(s0, a.mod_x);
@@ -249,10 +273,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     uint32_t m = fastmod(vy * sy0, a.mod_y) * (uint32_t)a.my +
                                  fastmod(vx * sx0, a.mod_x) * (uint32_t)a.mx;
                     if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
+                    if (kTabSmem) {
+                        const uint32_t b = tab_s + m * 8u;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {   // independent of each other: no serial chain
-                        const uint32_t mj = m + dxj[j];
-                        mm[j] = (mj >= (uint32_t)a.lcm) ? mj - (uint32_t)a.lcm : mj;
+                        for (int j = 0; j < 16; ++j) mm[j] = b + dxj[j];   // entry m + d < 2 lcm
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const uint32_t mj = m + dxj[j];
+                            mm[j] = (mj >= (uint32_t)a.lcm) ? mj - (uint32_t)a.lcm : mj;
+                        }
                     }
                 } else {
 #pragma unroll
@@ -262,7 +292,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                         const uint32_t sx = s - sy * (uint32_t)a.Sx;
                         uint32_t m = fastmod(vy * sy, a.mod_y) * (uint32_t)a.my +
                                      fastmod(vx * sx, a.mod_x) * (uint32_t)a.mx;
-                        mm[j] = (m >= (uint32_t)a.lcm) ? m - (uint32_t)a.lcm : m;
+                        m = (m >= (uint32_t)a.lcm) ? m - (uint32_t)a.lcm : m;
+                        mm[j] = kTabSmem ? tab_s + m * 8u : m;
                     }
                 }
             }
@@ -272,7 +303,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             for (int c = 0; c < 2; ++c) {
                 uint2 q[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) q[e] = vok ? tab[mm[c * 8 + e]] : make_uint2(0u, 0u);
+                for (int e = 0; e < 8; ++e) q[e] = kTabSmem ? lds_u2(mm[c * 8 + e]) : gtab[mm[c * 8 + e]];
                 uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -306,7 +337,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 }
                 if (s_abort) break;
                 mbar_arrive_tx(&fullC[sc], cStageBytes);
-                tma_load_1d(c_base + (size_t)sc * cStageBytes, src + (size_t)it * cStageBytes,
+                tma_load_1d(c_base + (size_t)sc * cStageBytes, src + (size_t)stage_of(it) * cStageBytes,
                             cStageBytes, &fullC[sc]);
             }
         }
@@ -377,23 +408,39 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             }
             epilogue_barrier();
             if (go) {
+                // Each warp updates rows vr = warp + 8 i of the tile, a lane two coefficients
+                // per row; the H values of 8 rows are loaded before any is stored, so the loads
+                // overlap instead of waiting on each other's stores.
                 const float2* Thi = reinterpret_cast<const float2*>(e_base);
                 const float2* Tlo = Thi + (size_t)kTileV * 64;
-                for (int vr = warp; vr < kTileV; vr += 8) {
-                    const int vv = v0 + vr;
-                    if (vv >= a.S) continue;
+                for (int vb = 0; vb < kTileV / 8; vb += 8) {
+                    float2 hv[8][2];
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int kl = hh * 32 + lane;
-                        const int k = k0 + j * 64 + kl;
-                        if (k < a.K) {
-                            const float2 x = Thi[(size_t)vr * 64 + kl], y = Tlo[(size_t)vr * 64 + kl];
-                            const float sc = s_scale[j * 64 + kl];
-                            float2* h = a.H + (size_t)vv * a.K + k;
-                            float2 hv = *h;
-                            hv.x = fmaf(x.x + y.x, sc, hv.x);
-                            hv.y = fmaf(x.y + y.y, sc, hv.y);
-                            *h = hv;
+                    for (int i = 0; i < 8; ++i) {
+                        const int vv = v0 + warp + 8 * (vb + i);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int k = k0 + j * 64 + hh * 32 + lane;
+                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                                                              : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int vr = warp + 8 * (vb + i);
+                        const int vv = v0 + vr;
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int kl = hh * 32 + lane;
+                            const int k = k0 + j * 64 + kl;
+                            if (vv < a.S && k < a.K) {
+                                const float2 x = Thi[(size_t)vr * 64 + kl], y = Tlo[(size_t)vr * 64 + kl];
+                                const float sc = s_scale[j * 64 + kl];
+                                float2 h = hv[i][hh];
+                                h.x = fmaf(x.x + y.x, sc, h.x);
+                                h.y = fmaf(x.y + y.y, sc, h.y);
+                                a.H[(size_t)vv * a.K + k] = h;
+                            }
                         }
                     }
                 }
@@ -473,22 +520,33 @@ cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cud
 bool split_path_available() { return true; }
 
 cudaError_t prepare_split_kernels() {
-    return allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<true>));
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<false>));
+    return e;
 }
 
 // Coefficients per CTA: 64 (one hi/lo m-tile) or 128 (two).
 int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
 
 // Pipeline depths for a tile width NT within the shared-memory budget.  The E region must hold
-// the two epilogue tiles (128 KB), so it keeps 4 stages; C takes what is left, up to 8.
+// the two epilogue tiles (128 KB), so it keeps 4 stages; C takes what is left, up to 8, after
+// the doubled phase table, which stays in shared memory whenever 3 or more C stages still fit.
 static void split_stages(int NT, int lcm, int* se, int* sc, int* tab) {
     const size_t limit = 226 * 1024 - 1024;   // dynamic bytes after the alignment slack
     const int E = 4;
+    for (int C = 8; C >= 3; --C)
+        if (tc_layout(NT, E, C, lcm, 1).total <= limit) {
+            *se = E;
+            *sc = C;
+            *tab = 1;
+            return;
+        }
     int C = 8;
     while (C > 2 && tc_layout(NT, E, C, lcm, 0).total > limit) --C;
     *se = E;
     *sc = C;
-    *tab = tc_layout(NT, E, C, lcm, 1).total <= limit ? 1 : 0;
+    *tab = 0;
 }
 
 size_t split_smem_bytes(int NT) {
@@ -538,12 +596,16 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.stages_total = n_pad / kChunk;
     a.tmem_cols = 2 * kTileV * (NT / 64);   // 256 or 512 columns
     a.wait_ns = kDeviceWaitNs;
+    a.rotate = 1;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
     split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_in_smem);
     const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_in_smem).total;
     dim3 grid((P->S + kTileV - 1) / kTileV, Kp / NT);
-    accumulate_tc_kernel<<<grid, kThreadsTC, smem, st>>>(a);
+    if (a.tab_in_smem)
+        accumulate_tc_kernel<true><<<grid, kThreadsTC, smem, st>>>(a);
+    else
+        accumulate_tc_kernel<false><<<grid, kThreadsTC, smem, st>>>(a);
     return cudaGetLastError();
 }
 

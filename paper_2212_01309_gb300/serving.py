@@ -6,8 +6,9 @@ batches arrive over time.  The loop:
 
   * admits waiting sessions first-fit whenever the HBM budget has room for their plan
     (wdd_plan_footprint); a finished session's memory is returned and the next ones start;
-  * coalesces each admitted session's contiguous pending batches into one push on that session's
-    stream, so the work of different sessions overlaps on the device;
+  * coalesces each admitted session's contiguous pending batches into pushes on that session's
+    stream, cut at its snapshot points, so the work of different sessions overlaps on the
+    device;
   * every `snapshot_every` frames of a session accumulates the staged frames (wdd_flush) and
     replays the session's captured CUDA graph of the reconstruction (deconvolution and inverse
     DFT), recording an event;
@@ -135,26 +136,35 @@ class Server:
         self.waiting = still
 
     def _service(self, lv: _Live) -> int:
-        """Pushes the session's contiguous pending batches; snapshots when due."""
+        """Pushes the session's contiguous pending batches, cut at its snapshot points, and
+        snapshots every `snapshot_every` frames."""
         actions = 0
-        while lv.pending:
-            t0, start, count = lv.pending[0]
-            if start != lv.pushed:
-                break                      # a gap: wait for the missing frames
-            run = [lv.pending.popleft()]
-            end = start + count
+        while lv.pending and lv.pending[0][1] == lv.pushed:
+            run = []                       # contiguous requests: [t_arrival, frames left]
+            end = lv.pushed
             while lv.pending and lv.pending[0][1] == end:
-                run.append(lv.pending.popleft())
-                end += run[-1][2]
-            idx = np.arange(start, end, dtype=np.int32)
-            lv.plan.push(lv.spec.frames[start:end], idx, stream=lv.stream)
+                t, _, c = lv.pending.popleft()
+                run.append([t, c])
+                end += c
+            pos, i = lv.pushed, 0
+            while pos < end:
+                piece_end = min(end, pos + self.snapshot_every - lv.since_snap)
+                need = piece_end - pos
+                while need > 0:            # attribute the piece's frames to their requests
+                    take = min(run[i][1], need)
+                    lv.unsnapped.append((run[i][0], take))
+                    run[i][1] -= take
+                    need -= take
+                    if run[i][1] == 0:
+                        i += 1
+                idx = np.arange(pos, piece_end, dtype=np.int32)
+                lv.plan.push(lv.spec.frames[pos:piece_end], idx, stream=lv.stream)
+                lv.since_snap += piece_end - pos
+                pos = piece_end
+                actions += 1
+                if lv.since_snap >= self.snapshot_every:
+                    lv.snapshot(final=False)
             lv.pushed = end
-            for t, _, c in run:
-                lv.unsnapped.append((t, c))
-                lv.since_snap += c
-            actions += 1
-            if lv.since_snap >= self.snapshot_every:
-                lv.snapshot(final=False)
         if lv.pushed == lv.spec.n_frames and not lv.closing:
             lv.snapshot(final=True)
             lv.closing = True
