@@ -46,14 +46,14 @@ def _env_int(name, default):
         return default
 
 
-def _traffic(stage: str):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu record, or None when
-    the kernel's source has changed since the capture."""
+def _traffic(kernel: str):
+    """DRAM bytes per launch of a kernel from the committed ncu record, or None when the
+    kernel's source has changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f).get(stage)
+            rec = json.load(f).get(kernel)
         if not rec:
             return None
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
@@ -393,6 +393,7 @@ def main(argv=None) -> int:
 
     # ---- roofline of the dominant kernel --------------------------------------------------
     peaks = _peaks()
+    proj_kernel = "project_tc_kernel" if opt.info()["proj_tensor"] else "project_kernel"
     frames_bytes = acq.det * acq.det * np.dtype(acq.np_dtype).itemsize
     K = rc["rank_k"]
     stage_ms = {k: v[0] for k, v in st.items()}
@@ -405,7 +406,7 @@ def main(argv=None) -> int:
         if path == "split":
             roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
                     "frac": ach / peaks["bf16"], "traffic": None,
-                    "note": f"algorithmic 4*S*K flops per frame; executed = 3x (split); peak "
+                    "note": f"algorithmic 4*S*K flops per frame; executed = 4x (split); peak "
                             f"= {peaks['src']} bf16 dense (fp16 same rate)"}
         else:
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS,
@@ -414,7 +415,7 @@ def main(argv=None) -> int:
     elif dom == "project":
         bpl = B * frames_bytes
         ach = bpl / (ms_launch * 1e-3) / 1e9
-        tr = _traffic("project")
+        tr = _traffic(proj_kernel)
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
                 "frac": ach / peaks["hbm"],
                 "traffic": (tr["bytes_per_launch"] * B / tr["frames_per_launch"]) if tr else None,
@@ -427,13 +428,15 @@ def main(argv=None) -> int:
         ach = bpl / (ms_launch * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
                 "frac": ach / peaks["hbm"], "traffic": None}
-    roof["kernel"] = dom
+    roof["kernel"] = proj_kernel if dom == "project" else dom
     roof["launch_ms"] = ms_launch
     # the tensor-core accumulation, whatever the dominant kernel
     acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1])
     acc_alg = 4.0 * S * K * ACCUM_DEPTH / (acc_ms * 1e-3) / 1e12
+    tr_acc = _traffic("accumulate_tc_kernel") if path == "split" else None
     roof_acc = {"bound": "tensor", "kernel": "split_coeff + accumulate_tc" if path == "split"
                 else "accumulate_fp32", "launch_ms": acc_ms,
+                "traffic": tr_acc["bytes_per_launch"] if tr_acc else None,
                 "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * (4 if path == "split" else 1),
                 "peak": peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac_algorithmic": acc_alg / (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),

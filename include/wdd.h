@@ -180,6 +180,10 @@ typedef struct {
     int64_t kernel_launches; /* hot-path kernel launches since the plan was created          */
     int32_t staged;          /* frames projected but not yet accumulated                     */
     int32_t finished;
+    int32_t proj_tensor;     /* 1: frames are projected on the tensor cores (split precision,
+                                real basis, uint16/float32 frames, det_x a multiple of 16);
+                                0: on the SIMT cores in FP32                                  */
+    int32_t reserved0;
 } wdd_plan_info;
 
 /* Reports the plan's derived constants and counters (host-side, no GPU work). */
@@ -206,7 +210,9 @@ wdd_status wdd_get_stage_times(wdd_plan* plan, double* ms_out, int64_t* launches
 /* Synchronises the plan's stream and reports whether any of its kernels gave up a bounded
  * device wait (tensor-core pipeline barriers wait at most ~2 s).  Returns WDD_ERR_TIMEOUT and
  * clears the flag if one did; the CUDA context stays usable and the accumulator must be
- * considered invalid (wdd_reset). */
+ * considered invalid (wdd_reset).  Returns WDD_ERR_UNSUPPORTED (and clears the flag) when the
+ * tensor-core projection met a float32 frame value outside |I| <= 65504, the range of its FP16
+ * hi/lo split; the coefficients of that frame are then invalid. */
 wdd_status wdd_check_device(wdd_plan* plan);
 
 /* Runs the library's bounded device wait on a barrier that nothing completes, with a limit of

@@ -65,6 +65,7 @@ cudaError_t allow_max_dynamic_smem(const void* func) {
 cudaError_t prepare_kernels() {
     static cudaError_t status = [] {
         cudaError_t e = prepare_project_kernels();
+        if (e == cudaSuccess) e = prepare_project_tc_kernels();
         if (e == cudaSuccess) e = prepare_reconstruct_kernels();
         if (e == cudaSuccess) e = prepare_split_kernels();
         return e;
@@ -143,6 +144,7 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += 4LL * P->depth * P->K + 4LL * P->depth;            // staging
     b += 16LL * P->S;                                       // spectrum + DFT scratch
     b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
+    if (P->proj_tc) b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx);   // basis image
     return b;
 }
 
@@ -392,6 +394,11 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
             delete P;
             return fail(WDD_ERR_UNSUPPORTED, "detector width times basis order too large");
         }
+        // split precision projects on the tensor cores wherever that kernel applies
+        P->proj_tc = (p.precision == WDD_PREC_SPLIT &&
+                      proj_tc_supported(P->Nx, P->Lx, P->complex_basis, p.frame_dtype) &&
+                      proj_tc_smem_bytes(P->Ny, P->Nx, P->Ly, P->Lx, P->K) + 1024 <= lim)
+                         ? 1 : 0;
     }
     if (P->K > 4096) {
         delete P;
@@ -476,6 +483,7 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         WDD_ALLOC(P->d_scale_inv, Kp);
         WDD_ALLOC(P->d_colmax, P->K);
     }
+    if (P->proj_tc) WDD_ALLOC(P->d_bimg, proj_tc_bimg_halves(P->Nx, P->Lx));
 #undef WDD_ALLOC
 
     cudaStream_t s0 = nullptr;
@@ -495,6 +503,7 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         if ((e = launch_hg_basis(P->d_By, P->Ny, P->Ly, P->sigma, P->cy, s0))) return cbail(e, "HG basis");
         if ((e = launch_hg_basis(P->d_Bx, P->Nx, P->Lx, P->sigma, P->cx, s0))) return cbail(e, "HG basis");
     }
+    if (P->proj_tc && (e = launch_build_bimg(P, P->d_bimg, s0))) return cbail(e, "projection basis image");
     {
         std::vector<double2> by((size_t)P->Ny * P->Ly), bx((size_t)P->Nx * P->Lx);
         if ((e = cudaMemcpy(by.data(), P->d_By, 16 * by.size(), cudaMemcpyDeviceToHost))) return cbail(e, "basis copy");
@@ -654,6 +663,9 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
             // after all earlier work on the stream), or when the caller allowed overlap across
             // pushes
             const bool overlap = off > 0 || flushed || P->p.overlap_pushes != 0;
+            if (P->proj_tc && (reinterpret_cast<uintptr_t>(fsrc) & 15u) == 0)
+                return launch_project_tc(P, fsrc, P->p.frame_dtype, nb, overlap, ids, c_out, i_out,
+                                         st);
             return launch_project(P, fsrc, P->p.frame_dtype, nb, device_src, overlap, ids, c_out,
                                   i_out, st);
         });
@@ -723,6 +735,8 @@ wdd_status wdd_plan_get_info(const wdd_plan* P, wdd_plan_info* out) {
     out->kernel_launches = P->launches_total;
     out->staged = P->staged;
     out->finished = P->finished ? 1 : 0;
+    out->proj_tensor = P->proj_tc;
+    out->reserved0 = 0;
     return WDD_OK;
 }
 
@@ -758,6 +772,12 @@ wdd_status wdd_check_device(wdd_plan* P) {
     WDD_CUDA(cudaStreamSynchronize(P->stream));
     unsigned code = 0;
     WDD_CUDA(cudaMemcpy(&code, P->d_status, 4, cudaMemcpyDeviceToHost));
+    if (code == 9u) {
+        WDD_CUDA(cudaMemset(P->d_status, 0, 4));
+        return fail(WDD_ERR_UNSUPPORTED,
+                    "a float32 frame value is outside the FP16 split range |I| <= 65504 of the "
+                    "tensor-core projection (use the FP32 precision path for such frames)");
+    }
     if (code != 0) {
         WDD_CUDA(cudaMemset(P->d_status, 0, 4));
         char buf[96];

@@ -88,6 +88,8 @@ struct wdd_plan {
     float* d_scale_inv = nullptr;  // split path: [Kp] inverse power-of-two column scales
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
+    uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
+    int proj_tc = 0;               // 1: projection on the tensor cores
     int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
 
     // host bookkeeping (exact)
@@ -149,6 +151,15 @@ size_t proj_smem_bytes(const ProjGeom& g);
 cudaError_t launch_project(const wdd_plan* P, const void* frames, int dtype, int n,
                            bool device_src, bool overlap, const IndexBlock& idx, float* c_out,
                            int32_t* idx_out, cudaStream_t st);  // also folds |c| into d_colmax
+// Tensor-core projection (split precision, real basis, uint16/float32 frames, Nx % 16 == 0).
+bool proj_tc_supported(int Nx, int Lx, int complex_basis, int frame_dtype);
+size_t proj_tc_smem_bytes(int Ny, int Nx, int Ly, int Lx, int K);
+size_t proj_tc_bimg_halves(int Nx, int Lx);
+cudaError_t prepare_project_tc_kernels();
+cudaError_t launch_build_bimg(const wdd_plan* P, uint16_t* img, cudaStream_t st);
+cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, int n, bool overlap,
+                              const IndexBlock& idx, float* c_out, int32_t* idx_out,
+                              cudaStream_t st);
 cudaError_t launch_accumulate_fp32(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                    cudaStream_t st);
 // Device-side waits give up after this long and report WDD_ERR_TIMEOUT.

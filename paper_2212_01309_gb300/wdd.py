@@ -72,6 +72,7 @@ class PlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_int64), ("frames_seen", ctypes.c_int64),
         ("positions_covered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("staged", ctypes.c_int32), ("finished", ctypes.c_int32),
+        ("proj_tensor", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 

@@ -1,0 +1,109 @@
+"""Projection on the tensor cores (split precision) against the FP64 oracle's projection.
+
+The tensor-core projection splits the frame and the basis into FP16 hi and lo parts (uint16
+counts exactly), so its coefficients carry FP32-level error: each is held to 2e-6 relative L2
+over a batch, the level of the SIMT FP32 projection.  Shapes cover full and partial 64-column
+chunks and detector heights above and below one 128-row tile.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle.wdd_oracle as W
+import synth
+from wdd_harness import gpu_plan, oracle_params, rel_l2, to_source
+
+pytestmark = pytest.mark.gpu
+
+COEFF_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _acq(det, dtype, dose, seed, scan=(6, 7)):
+    c1, _ = synth.config("c1")
+    return dataclasses.replace(c1, scan_y=scan[0], scan_x=scan[1], obj_y=2 * scan[0] + det // 2,
+                               obj_x=2 * scan[1] + det // 2, det=det, defocus_m=3e-9,
+                               dtype=dtype, dose=dose, seed_noise=seed)
+
+
+CASES = [
+    # name, detector, frame type, dose (None: noise-free intensities), basis, K
+    ("u16_n128_hg64", 128, "u16", 1e4, "hg_tensor", 64),
+    ("f32_n96_noisefree_hg49", 96, "f32", None, "hg_tensor", 49),
+    ("u16_n144_energy100", 144, "u16", 3e3, "hg_energy", 100),
+    ("f32_n48_counts_energy30", 48, "f32", 5e2, "hg_energy", 30),
+    ("u16_n256_hg256", 256, "u16", 1e3, "hg_tensor", 256),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+@pytest.mark.parametrize("source", ["device", "pinned"])
+def test_tensor_projection_matches_oracle(torch_cuda, case, source):
+    name, det, dtype, dose, basis, k = case
+    acq = _acq(det, dtype, dose, seed=len(name))
+    F = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    ref = W.coefficients(F, W.build_plan(oracle_params(acq, basis, k)))
+    with gpu_plan(acq, basis, k, precision="split", max_batch=len(idx),
+                  accum_depth=len(idx)) as g:
+        assert g.info()["proj_tensor"] == 1
+        g.push(to_source(F, source), idx)
+        g.check_device()
+        c = g.copy_array("coeff")
+    assert c.shape == ref.shape
+    assert rel_l2(c, ref) < COEFF_TOL
+
+
+def test_sources_give_identical_coefficients(torch_cuda):
+    acq = _acq(128, "u16", 1e4, seed=5)
+    F = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    out = []
+    for source in ("device", "pinned", "pageable"):
+        with gpu_plan(acq, "hg_tensor", 64, precision="split", max_batch=len(idx),
+                      accum_depth=len(idx)) as g:
+            g.push(to_source(F, source), idx)
+            g.check_device()
+            out.append(g.copy_array("coeff"))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_path_selection(torch_cuda):
+    a = _acq(128, "u16", 1e4, seed=6)
+    with gpu_plan(a, "hg_tensor", 64, precision="split") as g:
+        assert g.info()["proj_tensor"] == 1
+    with gpu_plan(a, "hg_tensor", 64, precision="fp32") as g:
+        assert g.info()["proj_tensor"] == 0          # the plain path stays on the SIMT cores
+    b = _acq(40, "u16", 1e4, seed=7)
+    with gpu_plan(b, "hg_tensor", 16, precision="split") as g:
+        assert g.info()["proj_tensor"] == 0          # detector width not a multiple of 16
+    c = _acq(32, "f64", None, seed=8)
+    with gpu_plan(c, "hg_tensor", 16, precision="split") as g:
+        assert g.info()["proj_tensor"] == 0          # float64 frames
+
+
+def test_out_of_range_float_frame_is_reported(torch_cuda):
+    """A float32 value beyond the FP16 split range sets the device status word: the check
+    reports it as unsupported, clears it, and the plan keeps working."""
+    from paper_2212_01309_gb300 import wdd
+    acq = _acq(64, "f32", 1e3, seed=9)
+    F = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    bad = F[:4].copy()
+    bad[2, 10, 20] = 1.0e5
+    with gpu_plan(acq, "hg_tensor", 16, precision="split", max_batch=64) as g:
+        g.push(to_source(bad, "device"), idx[:4])
+        with pytest.raises(wdd.WddError) as ei:
+            g.check_device()
+        assert ei.value.status == wdd.ERR_UNSUPPORTED
+        g.check_device()                             # cleared
+        g.reset()
+        g.push(to_source(F, "device"), idx)
+        g.check_device()
