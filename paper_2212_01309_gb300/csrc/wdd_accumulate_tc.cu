@@ -110,7 +110,7 @@ struct TcArgs {
     const uint2* tw16;        // [lcm] (re_hi | re_lo << 16, im_hi | im_lo << 16)
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
-    int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_in_smem;
+    int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_mode;
     int stagesE, stagesC;     // pipeline depths (E: generated phase factors, C: coefficients)
     int rotate;               // 1: each CTA starts at its own stage (see below)
     uint64_t wait_ns;
@@ -130,7 +130,9 @@ __host__ __device__ inline TcLayout tc_layout(int NT, int stagesE, int stagesC, 
     L.tmem = L.bar + 8 * (size_t)(2 * stagesE + 2 * stagesC + 1);
     L.scale = (L.tmem + 16 + 15) & ~size_t(15);
     L.tab = (L.scale + 4 * (size_t)NT + 15) & ~size_t(15);
-    L.total = L.tab + (tab ? 16 * (size_t)lcm : 0);   // the table twice over: index m + d < 2 lcm
+    // tab: 0 none (global), 1 the table twice over (index m + d < 2 lcm), 2 that doubled table
+    // in 16 interleaved copies, one per bank pair
+    L.total = L.tab + (tab == 1 ? 16 * (size_t)lcm : tab == 2 ? 256 * (size_t)lcm : 0);
     return L;
 }
 
@@ -146,17 +148,22 @@ __device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
     return v;
 }
 
-// kTabSmem: the phase table sits in shared memory twice over (entries m and m + lcm equal), so
-// the fast path adds a frame's phase step to a byte address with no reduction mod lcm; otherwise
-// the table is read from global memory with reduced indices.
-template <bool kTabSmem>
+// kTab > 0: the phase table sits in shared memory twice over (entries m and m + lcm equal), so
+// the fast path adds a frame's phase step to a byte address with no reduction mod lcm; with
+// kTab == 2 the doubled table is stored in 16 interleaved copies (entry e, copy c at 8 (16 e + c)
+// bytes) and lane l reads copy l % 16, so the 16 lanes of a half-warp always hit 16 different
+// bank pairs, whatever entries they look up.  kTab == 0: the table is read from global memory
+// with reduced indices.
+template <int kTab>
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NT = a.NT;                 // coefficients per CTA (64 or 128)
     const int MT = NT / 64;              // 128-row coefficient tiles (hi rows 0-63, lo rows 64-127)
     const int SE = a.stagesE, SC = a.stagesC;
-    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, kTabSmem ? 1 : 0);
+    constexpr bool kTabSmem = kTab > 0;
+    constexpr uint32_t kEntryBytes = kTab == 2 ? 128u : 8u;   // stride of the table index
+    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, kTab);
     const int cStageBytes = MT * 2 * kCMTileKStep;
     uint8_t* e_base = base + L.e;
     uint8_t* c_base = base + L.c;
@@ -199,9 +206,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         int k = k0 + t;
         s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
     }
-    if (kTabSmem)
+    if (kTab == 1)
         for (int t = threadIdx.x; t < 2 * a.lcm; t += blockDim.x)
             s_tab[t] = a.tw16[t < a.lcm ? t : t - a.lcm];
+    if (kTab == 2)
+        for (int t = threadIdx.x; t < 32 * a.lcm; t += blockDim.x) {
+            const int e = t >> 4;
+            s_tab[t] = a.tw16[e < a.lcm ? e : e - a.lcm];
+        }
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -231,12 +243,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             uint32_t acc = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                dxj[j] = kTabSmem ? acc * 8u : acc;
+                dxj[j] = kTabSmem ? acc * kEntryBytes : acc;
                 acc += dx;
                 if (acc >= (uint32_t)a.lcm) acc -= (uint32_t)a.lcm;
             }
         }
-        const uint32_t tab_s = smem_u32(s_tab);
+        const uint32_t tab_s = smem_u32(s_tab) + (kTab == 2 ? (uint32_t)(lane & 15) * 8u : 0u);
         // first and last frame index of this thread's K-step, prefetched one stage ahead
         const int32_t* ip0 = a.idx + (size_t)stage_of(0) * kChunk + kstep * 16;
         int32_t nf = __ldg(ip0), nl = __ldg(ip0 + 15);
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                                  fastmod(vx * sx0, a.mod_x) * (uint32_t)a.mx;
                     if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
                     if (kTabSmem) {
-                        const uint32_t b = tab_s + m * 8u;
+                        const uint32_t b = tab_s + m * kEntryBytes;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) mm[j] = b + dxj[j];   // entry m + d < 2 lcm
                     } else {
@@ -293,7 +305,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                         uint32_t m = fastmod(vy * sy, a.mod_y) * (uint32_t)a.my +
                                      fastmod(vx * sx, a.mod_x) * (uint32_t)a.mx;
                         m = (m >= (uint32_t)a.lcm) ? m - (uint32_t)a.lcm : m;
-                        mm[j] = kTabSmem ? tab_s + m * 8u : m;
+                        mm[j] = kTabSmem ? tab_s + m * kEntryBytes : m;
                     }
                 }
             }
@@ -343,34 +355,43 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         }
     } else {
         // ---------------- MMA issuer: D_j[coefficient row][Re v | Im v] --------------------
+        // With one coefficient tile the E_hi and E_lo products go to two accumulators (added in
+        // the epilogue), so consecutive MMAs do not wait on each other's accumulation.
+        // Descriptors are formed once and advanced by the byte offsets of stages and K-steps.
         if (lane == 0) {
             const uint32_t idesc = instr_desc(128, 2 * kTileV);
+            const uint64_t de0 = smem_desc(smem_u32(e_base), 128, 256);
+            const uint64_t dc0 = smem_desc(smem_u32(c_base), 128, 256);
+            const int nacc = MT == 1 ? 2 : 1;
             uint32_t acc = 0;
+            int st = 0, sc = 0;
+            uint32_t pe = 0, pc = 0;
             for (int it = 0; it < a.stages_total; ++it) {
-                const int st = it % SE, sc = it % SC;
-                if (!mbar_wait(&fullC[sc], (it / SC) & 1, a.wait_ns) ||
-                    !mbar_wait(&fullE[st], (it / SE) & 1, a.wait_ns)) {
+                if (!mbar_wait(&fullC[sc], pc, a.wait_ns) || !mbar_wait(&fullE[st], pe, a.wait_ns)) {
                     atomicExch(a.status, 3u);
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t se = smem_u32(e_base + (size_t)st * kEStageBytes);
-                const uint32_t sca = smem_u32(c_base + (size_t)sc * cStageBytes);
+                const uint64_t de = de0 + (uint64_t)((st * kEStageBytes) >> 4);
+                const uint64_t dc = dc0 + (uint64_t)((sc * cStageBytes) >> 4);
 #pragma unroll
                 for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    const uint64_t e_h = smem_desc(se + ks * kEKStepBytes, 128, 256);
-                    const uint64_t e_l = smem_desc(se + (2 + ks) * kEKStepBytes, 128, 256);
+                    const uint64_t e_h = de + (uint64_t)((ks * kEKStepBytes) >> 4);
+                    const uint64_t e_l = e_h + (uint64_t)((2 * kEKStepBytes) >> 4);
                     for (int j = 0; j < MT; ++j) {
-                        const uint64_t cd = smem_desc(sca + (j * 2 + ks) * kCMTileKStep, 128, 256);
-                        const uint32_t d = tmem + (uint32_t)(j * 2 * kTileV);
+                        const uint64_t cd = dc + (uint64_t)(((j * 2 + ks) * kCMTileKStep) >> 4);
+                        const uint32_t d = tmem + (uint32_t)(j * nacc * 2 * kTileV);
                         mma_f16(d, cd, e_h, idesc, acc);
-                        mma_f16(d, cd, e_l, idesc, 1u);
+                        mma_f16(d + (uint32_t)((nacc - 1) * 2 * kTileV), cd, e_l, idesc,
+                                nacc == 2 ? acc : 1u);
                     }
                     acc = 1u;
                 }
                 mma_commit(&emptyE[st]);   // free both stages once these MMAs have read them
                 mma_commit(&emptyC[sc]);
+                if (++st == SE) { st = 0; pe ^= 1u; }
+                if (++sc == SC) { sc = 0; pc ^= 1u; }
             }
             mma_commit(done);              // all issued MMAs complete -> epilogue
         }
@@ -394,14 +415,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         const int half = warp >> 2;                   // which half of the v columns
         const int krow = (quarter & 1) * 32 + lane;   // coefficient within the m-tile
         float2* T = reinterpret_cast<float2*>(e_base) + (size_t)(quarter >> 1) * kTileV * 64;
+        const int nacc = MT == 1 ? 2 : 1;
         for (int j = 0; j < MT; ++j) {
             if (go) {
                 const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                           (uint32_t)(j * 2 * kTileV);
+                                           (uint32_t)(j * nacc * 2 * kTileV);
                 for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
                     float re[16], im[16];
                     tmem_ld16(lane_addr + (uint32_t)c0, re);
                     tmem_ld16(lane_addr + (uint32_t)(kTileV + c0), im);
+                    if (nacc == 2) {   // E_lo products in the second accumulator
+                        float re2[16], im2[16];
+                        tmem_ld16(lane_addr + (uint32_t)(2 * kTileV + c0), re2);
+                        tmem_ld16(lane_addr + (uint32_t)(3 * kTileV + c0), im2);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            re[i] += re2[i];
+                            im[i] += im2[i];
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < 16; ++i) T[(size_t)(c0 + i) * 64 + krow] = make_float2(re[i], im[i]);
                 }
@@ -520,9 +552,11 @@ cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cud
 bool split_path_available() { return true; }
 
 cudaError_t prepare_split_kernels() {
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<true>));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<0>));
     if (e == cudaSuccess)
-        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<false>));
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<1>));
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<2>));
     return e;
 }
 
@@ -531,17 +565,19 @@ int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
 
 // Pipeline depths for a tile width NT within the shared-memory budget.  The E region must hold
 // the two epilogue tiles (128 KB), so it keeps 4 stages; C takes what is left, up to 8, after
-// the doubled phase table, which stays in shared memory whenever 3 or more C stages still fit.
+// the phase table.  The table goes to shared memory in the best form that leaves 3 or more C
+// stages: the bank-interleaved copies, else the doubled table; otherwise it stays in global.
 static void split_stages(int NT, int lcm, int* se, int* sc, int* tab) {
     const size_t limit = 226 * 1024 - 1024;   // dynamic bytes after the alignment slack
     const int E = 4;
-    for (int C = 8; C >= 3; --C)
-        if (tc_layout(NT, E, C, lcm, 1).total <= limit) {
-            *se = E;
-            *sc = C;
-            *tab = 1;
-            return;
-        }
+    for (int mode = 2; mode >= 1; --mode)
+        for (int C = 8; C >= 3; --C)
+            if (tc_layout(NT, E, C, lcm, mode).total <= limit) {
+                *se = E;
+                *sc = C;
+                *tab = mode;
+                return;
+            }
     int C = 8;
     while (C > 2 && tc_layout(NT, E, C, lcm, 0).total > limit) --C;
     *se = E;
@@ -594,18 +630,20 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.my = P->lcm / P->Sy;
     a.mx = P->lcm / P->Sx;
     a.stages_total = n_pad / kChunk;
-    a.tmem_cols = 2 * kTileV * (NT / 64);   // 256 or 512 columns
+    a.tmem_cols = 4 * kTileV;   // two 256-column accumulators (E_hi / E_lo parts, or two tiles)
     a.wait_ns = kDeviceWaitNs;
     a.rotate = 1;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
-    split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_in_smem);
-    const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_in_smem).total;
+    split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_mode);
+    const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_mode).total;
     dim3 grid((P->S + kTileV - 1) / kTileV, Kp / NT);
-    if (a.tab_in_smem)
-        accumulate_tc_kernel<true><<<grid, kThreadsTC, smem, st>>>(a);
+    if (a.tab_mode == 2)
+        accumulate_tc_kernel<2><<<grid, kThreadsTC, smem, st>>>(a);
+    else if (a.tab_mode == 1)
+        accumulate_tc_kernel<1><<<grid, kThreadsTC, smem, st>>>(a);
     else
-        accumulate_tc_kernel<false><<<grid, kThreadsTC, smem, st>>>(a);
+        accumulate_tc_kernel<0><<<grid, kThreadsTC, smem, st>>>(a);
     return cudaGetLastError();
 }
 
