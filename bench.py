@@ -64,6 +64,28 @@ def _traffic(kernel: str):
         return None
 
 
+def dist_env():
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 without one)."""
+    return _env_int("WORLD_SIZE", 1), _env_int("RANK", 0), _env_int("LOCAL_RANK", 0)
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest value over all ranks: with per-rank step times, the slowest rank's."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job rate: every rank processes its own units (replicas, weak scaling), so the job
+    completes world x units per step in the slowest rank's step time."""
+    return units_per_rank * world / (ms_per_step * 1e-3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -195,33 +217,55 @@ def run_serving(args) -> int:
 
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
     mix = synth.serving_mix()
-    sessions = []
+    sessions, plain = [], []
     for sid, (acq, rc) in enumerate(mix):
         frames = TorchFrames(acq).all()
         p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
                                         epsilon=rc["epsilon"], precision="split", max_batch=512,
                                         accum_depth=2048, overlap_pushes=True)
         sessions.append(serving.Session(sid=sid, params=p, frames=frames, n_frames=acq.n_frames))
+        # the plain path for the same session: FP32 SIMT kernels, every push accumulated at once
+        q = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                        epsilon=rc["epsilon"], precision="fp32", max_batch=512,
+                                        accum_depth=0)
+        plain.append(serving.Session(sid=sid, params=q, frames=frames, n_frames=acq.n_frames))
     torch.cuda.synchronize()
     arrivals = synth.serving_arrivals([s.n_frames for s in sessions])
     free, total = torch.cuda.mem_get_info()
     budget = int(min(free * 0.5, 64 << 30))
+    deadline = 0.02
     out = {"mode": "serving", "metric": METRIC, "unit": UNIT, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "6 sessions: scan/detector 64^2/64^2, 128^2/64^2, 128^2/128^2, "
                                   "256^2/128^2, 192x256/96^2, 256^2/256^2; uint16 Poisson frames; "
                                   "batches of 16-512 frames; snapshot every 1024 frames per session",
                       "arrival_rate_fps": 20000, "frames": sum(s.n_frames for s in sessions),
                       "schedule_s": arrivals[-1][0], "hbm_budget_bytes": budget,
-                      "precision": "split", "cuda_graph_snapshots": True}}
-    for mode in ("open_loop", "closed_loop"):
-        srv = serving.Server(hbm_budget_bytes=budget, snapshot_every=1024, use_graphs=True)
-        for s in sessions:
+                      "precision": "split", "cuda_graph_snapshots": True,
+                      "deadline_run_snapshot_max_delay_ms": deadline * 1e3}}
+    results = {}
+    runs = [("open_loop", sessions, True, None), ("open_loop_deadline", sessions, True, deadline),
+            ("closed_loop", sessions, False, None), ("closed_loop_fp32_plain", plain, False, None)]
+    for mode, specs, open_loop, delay in runs:
+        srv = serving.Server(hbm_budget_bytes=budget, snapshot_every=1024, use_graphs=True,
+                             snapshot_max_delay_s=delay)
+        for s in specs:
             srv.add_session(s)
         setup = srv.admit_now()          # plans (Algorithm 1) built when the sessions are set up
         torch.cuda.synchronize()
-        st = srv.run(arrivals, open_loop=(mode == "open_loop"), timeout_s=1800)
+        st = srv.run(arrivals, open_loop=open_loop, timeout_s=1800)
         st["session_setup_s"] = setup
         out[mode] = st
+        results[mode] = srv.results
+
+    def rel(a, b):   # relative L2 of mean-subtracted phases
+        a = a.astype(np.float64) - a.mean()
+        b = b.astype(np.float64) - b.mean()
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["closed_loop"]["phase_rel_l2_vs_fp32_plain_max"] = max(
+        rel(results["closed_loop"][sid], results["closed_loop_fp32_plain"][sid])
+        for sid in results["closed_loop"])
+    out["closed_loop"]["speedup_vs_fp32_plain"] = (out["closed_loop"]["frames_per_s"] /
+                                                   out["closed_loop_fp32_plain"]["frames_per_s"])
     out["value"] = out["closed_loop"]["frames_per_s"]
     print(json.dumps(out), flush=True)
     return 0
@@ -254,9 +298,7 @@ def main(argv=None) -> int:
     import synth
     from paper_2212_01309_gb300 import wdd
 
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
+    world, rank, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -319,11 +361,7 @@ def main(argv=None) -> int:
         e1.synchronize()
         ms = e0.elapsed_time(e1) / k
         barrier()
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ms, world, device="cuda")
 
     with torch.cuda.stream(stream):
         # ---- plain FP32 path (eager, every push accumulated at once) -------------------------
@@ -398,8 +436,12 @@ def main(argv=None) -> int:
     K = rc["rank_k"]
     stage_ms = {k: v[0] for k, v in st.items()}
     dom = max(stage_ms, key=stage_ms.get)
+    # launches per flush of the optimised path: the split pre-pass, then one accumulation launch
+    # per 1024 staged frames (the library's segment length)
+    per_flush = (1 + (ACCUM_DEPTH + 1023) // 1024) if path == "split" else 1
     ms_launch = st[dom][0] / max(1, st[dom][1])
     if dom == "accumulate":
+        ms_launch *= per_flush           # one flush of ACCUM_DEPTH frames
         n_per = ACCUM_DEPTH
         flops = 4.0 * S * K * n_per
         ach = flops / (ms_launch * 1e-3) / 1e12
@@ -431,11 +473,12 @@ def main(argv=None) -> int:
     roof["kernel"] = proj_kernel if dom == "project" else dom
     roof["launch_ms"] = ms_launch
     # the tensor-core accumulation, whatever the dominant kernel
-    acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1])
+    acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1]) * per_flush   # per flush
     acc_alg = 4.0 * S * K * ACCUM_DEPTH / (acc_ms * 1e-3) / 1e12
     tr_acc = _traffic("accumulate_tc_kernel") if path == "split" else None
-    roof_acc = {"bound": "tensor", "kernel": "split_coeff + accumulate_tc" if path == "split"
-                else "accumulate_fp32", "launch_ms": acc_ms,
+    roof_acc = {"bound": "tensor", "kernel": f"split_coeff + {per_flush - 1} x accumulate_tc "
+                f"(one flush of {ACCUM_DEPTH} frames)" if path == "split"
+                else "accumulate_fp32", "flush_ms": acc_ms,
                 "traffic": tr_acc["bytes_per_launch"] if tr_acc else None,
                 "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * (4 if path == "split" else 1),
                 "peak": peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -458,7 +501,7 @@ def main(argv=None) -> int:
     if rank == 0:
         lat_ms = np.array(lat) * 1e3
         out = {
-            "metric": METRIC, "value": S * world / (ms_opt * 1e-3), "unit": UNIT,
+            "metric": METRIC, "value": job_throughput(S, world, ms_opt), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_opt, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if path == "fp32" else "f16-split/f32",
@@ -469,7 +512,7 @@ def main(argv=None) -> int:
                        "overlap_pushes": True,
                        "cuda_graph": True,
                        "l2": "inputs larger than L2 (1.07 GB of frames per step)"},
-            "baseline_fp32_plain": {"value": S * world / (ms_plain * 1e-3), "unit": UNIT,
+            "baseline_fp32_plain": {"value": job_throughput(S, world, ms_plain), "unit": UNIT,
                                     "ms_per_step": ms_plain,
                                     "speedup": ms_plain / ms_opt,
                                     "phase_rel_l2_vs_plain": err},
@@ -480,7 +523,7 @@ def main(argv=None) -> int:
             "roofline": roof,
             "roofline_accumulate": roof_acc,
             "cpu_baseline": cpu,
-            "e2e": {"value": S * world / (ms_e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_throughput(S, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": int(S * frames_bytes + 4 * S),
                     "d2h_bytes_per_step": int(4 * S),
                     "note": "frames read by the kernels from pinned host memory; phase copied back"},

@@ -57,9 +57,11 @@ typedef enum { WDD_BASIS_FOURIER_FULL = 0, WDD_BASIS_HG_TENSOR = 1, WDD_BASIS_HG
 
 /* Arithmetic of the streaming steps.
  *  FP32   projection and phase accumulation in FP32 FMA on the SIMT cores.
- *  SPLIT  tensor-core accumulation: phase factors and coefficients split into hi + lo FP16
- *         parts, three products (hi*hi + lo*hi + hi*lo) accumulated in FP32.  Staged frames are
- *         accumulated accum_depth at a time. */
+ *  SPLIT  tensor cores: phase factors and coefficients split into hi + lo FP16 parts, all four
+ *         products accumulated in FP32 (the lo*lo term lies below FP32 rounding); frames and the
+ *         projection basis likewise on the tensor cores where the frame type and detector width
+ *         allow (see wdd_plan_info.proj_tensor).  Staged frames are accumulated accum_depth at a
+ *         time, in launches of accum_segment frames. */
 typedef enum { WDD_PREC_FP32 = 0, WDD_PREC_SPLIT = 1 } wdd_precision;
 
 /* Element type of the frames passed to wdd_push_frames. */
@@ -92,11 +94,16 @@ typedef struct {
                                  runs on the stream right before a push, e.g. frames written by
                                  a detector DMA or by copies.  Later chunks of one push always
                                  overlap (their predecessor is the push's own projection). */
-    int32_t reserved1;
+    int32_t accum_segment;    /* SPLIT: staged frames summed in the tensor cores' FP32 accumulators
+                                 per launch (rounded up to a multiple of 32); the launches' sums
+                                 are added into H in FP32.  The accumulator error grows linearly
+                                 with the segment (relative 3.2e-7 at 256 frames, 7.6e-7 at 1024,
+                                 3.8e-6 at 4096 on a 128x128 scan); longer segments run faster.
+                                 0 = 1024. */
 } wdd_params;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
- * N/2, relative epsilon 1e-3, no overlap across pushes.  Geometry fields are zeroed and must be
+ * N/2, relative epsilon 1e-3, no overlap across pushes, accum_segment 0 (1024).  Geometry fields are zeroed and must be
  * set by the caller. */
 wdd_status wdd_params_default(wdd_params* p);
 

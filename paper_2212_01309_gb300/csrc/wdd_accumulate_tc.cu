@@ -113,6 +113,8 @@ struct TcArgs {
     int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_mode;
     int stagesE, stagesC;     // pipeline depths (E: generated phase factors, C: coefficients)
     int rotate;               // 1: each CTA starts at its own stage (see below)
+    int ktile_stages;         // stages per coefficient k-tile in the split operand
+    int last;                 // 1: the last launch of a flush (resets the column maxima)
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         // ---------------- C loader (TMA), running up to SC stages ahead ----------------
         if (lane == 0) {
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
-                                 (size_t)blockIdx.y * a.stages_total * cStageBytes;
+                                 (size_t)blockIdx.y * a.ktile_stages * cStageBytes;
             for (int it = 0; it < a.stages_total; ++it) {
                 const int sc = it % SC;
                 if (it >= SC && !mbar_wait(&emptyC[sc], ((it / SC) - 1) & 1, a.wait_ns)) {
@@ -481,7 +483,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0)
-        for (int t = threadIdx.x; t < a.K; t += blockDim.x) a.colmax[t] = 0u;
+        if (a.last)
+            for (int t = threadIdx.x; t < a.K; t += blockDim.x) a.colmax[t] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 9) {
@@ -591,6 +594,12 @@ size_t split_smem_bytes(int NT) {
     return 1024 + tc_layout(NT, E, C, 1, 0).total;
 }
 
+// Kernel launches of one flush of n staged frames: the split pre-pass and one per segment.
+int split_launch_count(int n, int segment) {
+    const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
+    return 1 + (n_pad + segment - 1) / segment;
+}
+
 size_t split_coeff_bytes(int K, int depth_pad) {
     const int NT = split_tile_n(K);
     const int Kp = (K + NT - 1) / NT * NT;
@@ -638,12 +647,29 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_mode);
     const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_mode).total;
     dim3 grid((P->S + kTileV - 1) / kTileV, Kp / NT);
-    if (a.tab_mode == 2)
-        accumulate_tc_kernel<2><<<grid, kThreadsTC, smem, st>>>(a);
-    else if (a.tab_mode == 1)
-        accumulate_tc_kernel<1><<<grid, kThreadsTC, smem, st>>>(a);
-    else
-        accumulate_tc_kernel<0><<<grid, kThreadsTC, smem, st>>>(a);
+    // One launch per segment of at most P->segment staged frames: the tensor cores' FP32
+    // accumulation loses a little precision with every MMA added into an accumulator (error
+    // linear in the number added), so long flushes run as several launches whose sums are added
+    // into H in FP32 in between.
+    const int stages_all = n_pad / kChunk;
+    const int seg = P->segment / kChunk;
+    const size_t c_stage_halves = (size_t)(NT / 64) * kCMTileKStep;   // one stage of one k-tile
+    a.ktile_stages = stages_all;
+    for (int s0 = 0; s0 < stages_all; s0 += seg) {
+        TcArgs b = a;
+        b.stages_total = stages_all - s0 < seg ? stages_all - s0 : seg;
+        b.csplit = a.csplit + (size_t)s0 * c_stage_halves;
+        b.idx = idx + (size_t)s0 * kChunk;
+        b.last = s0 + seg >= stages_all ? 1 : 0;
+        if (b.tab_mode == 2)
+            accumulate_tc_kernel<2><<<grid, kThreadsTC, smem, st>>>(b);
+        else if (b.tab_mode == 1)
+            accumulate_tc_kernel<1><<<grid, kThreadsTC, smem, st>>>(b);
+        else
+            accumulate_tc_kernel<0><<<grid, kThreadsTC, smem, st>>>(b);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

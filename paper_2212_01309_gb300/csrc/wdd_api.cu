@@ -188,7 +188,9 @@ cudaError_t staged_launch(wdd_plan* P, int stage, int count, F&& launch) {
 
 wdd_status flush(wdd_plan* P) {
     if (P->staged == 0) return WDD_OK;
-    cudaError_t e = staged_launch(P, WDD_STAGE_ACCUMULATE, 1, [&] {
+    const int count =
+        P->p.precision == WDD_PREC_SPLIT ? split_launch_count(P->staged, P->segment) : 1;
+    cudaError_t e = staged_launch(P, WDD_STAGE_ACCUMULATE, count, [&] {
         return P->p.precision == WDD_PREC_SPLIT
                    ? launch_accumulate_split(P, P->d_cstage, P->d_idxstage, P->staged, P->stream)
                    : launch_accumulate_fp32(P, P->d_cstage, P->d_idxstage, P->staged, P->stream);
@@ -300,6 +302,8 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
     if (p.rank_k <= 0) return fail(WDD_ERR_INVALID_ARG, "rank_k must be positive");
     if (p.proj_cluster < 0 || p.proj_cluster > 8 || (p.proj_cluster & (p.proj_cluster - 1)))
         return fail(WDD_ERR_INVALID_ARG, "proj_cluster must be 0, 1, 2, 4 or 8");
+    if (p.accum_segment < 0 || p.accum_segment > 8192)
+        return fail(WDD_ERR_INVALID_ARG, "accum_segment must be in [0, 8192]");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -317,6 +321,7 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
     P->chunk = std::min(p.max_batch, kLaunchFrames);
     P->depth = p.accum_depth > 0 ? std::max(p.accum_depth, p.max_batch) : p.max_batch;
     P->depth_pad = (P->depth + 31) / 32 * 32;
+    P->segment = p.accum_segment > 0 ? (p.accum_segment + 31) / 32 * 32 : 1024;
     if (p.precision == WDD_PREC_SPLIT && P->depth_pad > 8192) {
         delete P;
         return fail(WDD_ERR_INVALID_ARG, "split precision stages at most 8192 frames");

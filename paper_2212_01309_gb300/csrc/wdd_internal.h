@@ -91,6 +91,7 @@ struct wdd_plan {
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
     int proj_tc = 0;               // 1: projection on the tensor cores
     int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
+    int segment = 1024;            // split path: frames per tensor-core accumulation launch
 
     // host bookkeeping (exact)
     std::vector<uint32_t> hits;
@@ -168,6 +169,7 @@ bool split_path_available();
 int split_tile_n(int K);
 size_t split_smem_bytes(int NT);
 size_t split_coeff_bytes(int K, int depth_pad);   // bytes of the split coefficient operand
+int split_launch_count(int n, int segment);       // kernel launches of a flush of n frames
 cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cudaStream_t st);
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st);

@@ -9,15 +9,17 @@ batches arrive over time.  The loop:
   * coalesces each admitted session's contiguous pending batches into pushes on that session's
     stream, cut at its snapshot points, so the work of different sessions overlaps on the
     device;
-  * every `snapshot_every` frames of a session accumulates the staged frames (wdd_flush) and
-    replays the session's captured CUDA graph of the reconstruction (deconvolution and inverse
-    DFT), recording an event;
+  * every `snapshot_every` frames of a session, and also whenever its oldest frame not yet in a
+    snapshot has waited `snapshot_max_delay_s` (a display refresh deadline, optional),
+    accumulates the staged frames (wdd_flush) and replays the session's captured CUDA graph of
+    the reconstruction (deconvolution and inverse DFT), recording an event;
   * measures each frame's latency from its arrival to the completion of the first snapshot that
     contains it.
 
-All GPU work goes through the C ABI of libwdd.so; this module is scheduling only.  Results do not
-depend on the mix: a session's frames are projected one by one and accumulated in the order they
-were pushed, with flushes only at its own snapshot points.
+All GPU work goes through the C ABI of libwdd.so; this module is scheduling only.  Without a
+deadline, results do not depend on the mix: a session's frames are projected one by one and
+accumulated in the order they were pushed, with flushes only at its own snapshot points.  With a
+deadline the flush points depend on timing, which changes only the FP32 rounding of the sums.
 """
 from __future__ import annotations
 
@@ -85,9 +87,11 @@ class Server:
     """Serving loop.  `hbm_budget_bytes` bounds the summed plan footprints of admitted sessions."""
 
     def __init__(self, hbm_budget_bytes: int | None = None, snapshot_every: int = 1024,
-                 use_graphs: bool = True, clock=time.perf_counter):
+                 use_graphs: bool = True, clock=time.perf_counter,
+                 snapshot_max_delay_s: float | None = None):
         self.budget = hbm_budget_bytes
         self.snapshot_every = snapshot_every
+        self.max_delay = snapshot_max_delay_s
         self.use_graphs = use_graphs
         self.clock = clock
         self.waiting: list[Session] = []
@@ -168,6 +172,10 @@ class Server:
         if lv.pushed == lv.spec.n_frames and not lv.closing:
             lv.snapshot(final=True)
             lv.closing = True
+            actions += 1
+        elif (self.max_delay is not None and lv.unsnapped and not lv.closing and
+              self.clock() - lv.unsnapped[0][0] >= self.max_delay):
+            lv.snapshot(final=False)
             actions += 1
         return actions
 

@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
         ("proj_cluster", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_int64),
         ("overlap_pushes", ctypes.c_int32),
-        ("reserved1", ctypes.c_int32),
+        ("accum_segment", ctypes.c_int32),
     ]
 
 
@@ -144,7 +144,8 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 semiconv_rad, defocus_m=0.0, epsilon=1e-3, rank_k, basis="hg_tensor",
                 precision="fp32", frame_dtype="f32", max_batch=256, accum_depth=0,
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
-                hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False) -> Params:
+                hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False,
+                accum_segment=0) -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -160,6 +161,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.hbm_budget_bytes = hbm_budget_bytes
     p.proj_cluster = proj_cluster
     p.overlap_pushes = 1 if overlap_pushes else 0
+    p.accum_segment = accum_segment
     return p
 
 

@@ -91,3 +91,26 @@ def test_smallest_session_matches_oracle(mix):
     p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
     _, ref = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
     assert phase_err(srv.results[0].astype(np.float64), ref) <= PHASE_TOL
+
+
+def test_deadline_snapshots_open_loop(mix):
+    """Open loop with a 5 ms snapshot deadline: many more snapshots at timing-dependent points;
+    every result stays within the FP32 tolerance of the deadline-free run, and the smallest
+    session still matches the oracle."""
+    from paper_2212_01309_gb300 import serving
+    sessions, arrivals = mix
+    ref, _ = _serve(sessions, arrivals)
+    srv = serving.Server(snapshot_every=256, use_graphs=True, snapshot_max_delay_s=0.005)
+    for _, _, s in sessions:
+        srv.add_session(s)
+    stats = srv.run(arrivals, open_loop=True, timeout_s=300)
+    assert stats["sessions"] == len(sessions)
+    assert stats["frames"] == sum(a.n_frames for a, _, _ in sessions)
+    for sid in ref.results:
+        assert phase_err(srv.results[sid].astype(np.float64),
+                         ref.results[sid].astype(np.float64)) <= PHASE_TOL
+    acq, rc, s = sessions[0]
+    frames = s.frames.cpu().numpy()
+    p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
+    _, ph = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
+    assert phase_err(srv.results[0].astype(np.float64), ph) <= PHASE_TOL
