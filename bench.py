@@ -261,9 +261,11 @@ def run_serving(args) -> int:
         a = a.astype(np.float64) - a.mean()
         b = b.astype(np.float64) - b.mean()
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    out["closed_loop"]["phase_rel_l2_vs_fp32_plain_max"] = max(
+    out["closed_loop"]["phase_rel_l2_vs_fp32_plain"] = [
         rel(results["closed_loop"][sid], results["closed_loop_fp32_plain"][sid])
-        for sid in results["closed_loop"])
+        for sid in sorted(results["closed_loop"])]
+    out["closed_loop"]["phase_std_per_session"] = [
+        float(results["closed_loop"][sid].std()) for sid in sorted(results["closed_loop"])]
     out["closed_loop"]["speedup_vs_fp32_plain"] = (out["closed_loop"]["frames_per_s"] /
                                                    out["closed_loop_fp32_plain"]["frames_per_s"])
     out["value"] = out["closed_loop"]["frames_per_s"]
@@ -479,7 +481,8 @@ def main(argv=None) -> int:
     roof_acc = {"bound": "tensor", "kernel": f"split_coeff + {per_flush - 1} x accumulate_tc "
                 f"(one flush of {ACCUM_DEPTH} frames)" if path == "split"
                 else "accumulate_fp32", "flush_ms": acc_ms,
-                "traffic": tr_acc["bytes_per_launch"] if tr_acc else None,
+                "traffic": (tr_acc["bytes_per_launch"] * ACCUM_DEPTH / tr_acc["frames_per_launch"])
+                           if tr_acc else None,
                 "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * (4 if path == "split" else 1),
                 "peak": peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac_algorithmic": acc_alg / (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),
