@@ -330,10 +330,11 @@ def main(argv=None) -> int:
                 raise
         path = "split" if split_ok else "fp32"
 
-    def mk(precision, depth, overlap):
+    def mk(precision, depth, overlap, mode="direct"):
         return wdd.Plan(wdd.params_from_acquisition(
             acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"],
-            precision=precision, max_batch=B, accum_depth=depth, overlap_pushes=overlap))
+            precision=precision, max_batch=B, accum_depth=depth, overlap_pushes=overlap,
+            accum_mode=mode))
 
     # the plain path: FP32 SIMT, every push accumulated at once, eager launches
     plain = mk("fp32", 0, False)
@@ -401,6 +402,19 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         st = opt.stage_times()
 
+        # ---- variant: scan-row factorised accumulation (not the paper's form), same step ----
+        sep = mk(path, ACCUM_DEPTH, True, mode="separable")
+        for _ in range(args.warmup):
+            step(sep, d_frames)
+        sgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(sgraph, stream=stream):
+            step(sep, d_frames)
+        for _ in range(args.warmup):
+            sgraph.replay()
+        ms_sep = timed(sgraph.replay, args.steps)
+        ph_sep = phase.clone()
+        sep.close()
+
         # ---- end to end through the public API from pinned host memory ---------------------
         def e2e_step():
             step(opt, h_frames)
@@ -427,9 +441,10 @@ def main(argv=None) -> int:
                 pending = []
     torch.cuda.synchronize()
 
-    err = float(np.linalg.norm((ph_opt - ph_opt.mean()).cpu().numpy() -
-                               (ph_plain - ph_plain.mean()).cpu().numpy()) /
-                np.linalg.norm((ph_plain - ph_plain.mean()).cpu().numpy()))
+    def phase_diff(a, b):
+        return float(np.linalg.norm((a - a.mean()).cpu().numpy() - (b - b.mean()).cpu().numpy()) /
+                     np.linalg.norm((b - b.mean()).cpu().numpy()))
+    err = phase_diff(ph_opt, ph_plain)
 
     # ---- roofline of the dominant kernel --------------------------------------------------
     peaks = _peaks()
@@ -519,6 +534,12 @@ def main(argv=None) -> int:
                                     "ms_per_step": ms_plain,
                                     "speedup": ms_plain / ms_opt,
                                     "phase_rel_l2_vs_plain": err},
+            "variant_separable": {"value": job_throughput(S, world, ms_sep), "unit": UNIT,
+                                  "ms_per_step": ms_sep,
+                                  "phase_rel_l2_vs_plain": phase_diff(ph_sep, ph_plain),
+                                  "note": "same step with the scan DFT factorised by rows "
+                                          "(accum_mode separable, FP32 SIMT): not the paper's "
+                                          "form, the same H up to rounding"},
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                            "p99": float(np.percentile(lat_ms, 99)),
                            "snapshot_every": LATENCY_SNAPSHOT_EVERY},

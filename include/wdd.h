@@ -64,6 +64,18 @@ typedef enum { WDD_BASIS_FOURIER_FULL = 0, WDD_BASIS_HG_TENSOR = 1, WDD_BASIS_HG
  *         time, in launches of accum_segment frames. */
 typedef enum { WDD_PREC_FP32 = 0, WDD_PREC_SPLIT = 1 } wdd_precision;
 
+/* How staged frames are added into the accumulator H.
+ *  DIRECT     H[v, k] += sum_s F_2D[v, s] c_s[k] over every scan frequency v for every frame
+ *             (Eq. 14, Algorithm 2): 4 S K flops per frame, on the tensor cores (SPLIT) or the
+ *             SIMT cores (FP32).
+ *  SEPARABLE  the scan DFT factorised by scan rows (not in the paper): for each scan row s_y
+ *             touched by the staged frames, G[v_x, k] = sum over its frames of
+ *             exp(-2 pi i v_x s_x / S_x) c_s[k], then H[(v_y, v_x), k] +=
+ *             sum over rows of exp(-2 pi i v_y s_y / S_y) G_{s_y}[v_x, k].  The same H up to
+ *             rounding, in 4 S_x K flops per frame plus 8 S K per touched row (64x fewer at a
+ *             128 x 128 scan in raster order); FP32 on the SIMT cores for either precision. */
+typedef enum { WDD_ACCUM_DIRECT = 0, WDD_ACCUM_SEPARABLE = 1 } wdd_accum_mode;
+
 /* Element type of the frames passed to wdd_push_frames. */
 typedef enum { WDD_FRAME_U16 = 0, WDD_FRAME_F32 = 1, WDD_FRAME_F64 = 2 } wdd_frame_dtype;
 
@@ -100,6 +112,8 @@ typedef struct {
                                  with the segment (relative 3.2e-7 at 256 frames, 7.6e-7 at 1024,
                                  3.8e-6 at 4096 on a 128x128 scan); longer segments run faster.
                                  0 = 1024. */
+    int32_t accum_mode;       /* wdd_accum_mode: how staged frames are added into H            */
+    int32_t reserved2;
 } wdd_params;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
@@ -190,7 +204,7 @@ typedef struct {
     int32_t proj_tensor;     /* 1: frames are projected on the tensor cores (split precision,
                                 real basis, uint16/float32 frames, det_x a multiple of 16);
                                 0: on the SIMT cores in FP32                                  */
-    int32_t reserved0;
+    int32_t accum_mode;      /* wdd_accum_mode of the plan                                   */
 } wdd_plan_info;
 
 /* Reports the plan's derived constants and counters (host-side, no GPU work). */

@@ -66,6 +66,7 @@ cudaError_t prepare_kernels() {
     static cudaError_t status = [] {
         cudaError_t e = prepare_project_kernels();
         if (e == cudaSuccess) e = prepare_project_tc_kernels();
+        if (e == cudaSuccess) e = prepare_rows_kernels();
         if (e == cudaSuccess) e = prepare_reconstruct_kernels();
         if (e == cudaSuccess) e = prepare_split_kernels();
         return e;
@@ -145,6 +146,10 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += 16LL * P->S;                                       // spectrum + DFT scratch
     b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
     if (P->proj_tc) b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx);   // basis image
+    if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) {                            // row slots, G
+        const int64_t R = rows_slots(P->Sy, P->depth_pad);
+        b += 8LL * R * P->Sx * P->K + 12LL * R + 4LL * P->depth_pad + 4;
+    }
     return b;
 }
 
@@ -188,9 +193,12 @@ cudaError_t staged_launch(wdd_plan* P, int stage, int count, F&& launch) {
 
 wdd_status flush(wdd_plan* P) {
     if (P->staged == 0) return WDD_OK;
-    const int count =
-        P->p.precision == WDD_PREC_SPLIT ? split_launch_count(P->staged, P->segment) : 1;
+    const bool rows = P->p.accum_mode == WDD_ACCUM_SEPARABLE;
+    const int count = rows ? 3
+                           : P->p.precision == WDD_PREC_SPLIT ? split_launch_count(P->staged, P->segment)
+                                                              : 1;
     cudaError_t e = staged_launch(P, WDD_STAGE_ACCUMULATE, count, [&] {
+        if (rows) return launch_accumulate_rows(P, P->d_cstage, P->d_idxstage, P->staged, P->stream);
         return P->p.precision == WDD_PREC_SPLIT
                    ? launch_accumulate_split(P, P->d_cstage, P->d_idxstage, P->staged, P->stream)
                    : launch_accumulate_fp32(P, P->d_cstage, P->d_idxstage, P->staged, P->stream);
@@ -304,6 +312,8 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         return fail(WDD_ERR_INVALID_ARG, "proj_cluster must be 0, 1, 2, 4 or 8");
     if (p.accum_segment < 0 || p.accum_segment > 8192)
         return fail(WDD_ERR_INVALID_ARG, "accum_segment must be in [0, 8192]");
+    if (p.accum_mode != WDD_ACCUM_DIRECT && p.accum_mode != WDD_ACCUM_SEPARABLE)
+        return fail(WDD_ERR_INVALID_ARG, "unknown accumulation mode");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -489,6 +499,15 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         WDD_ALLOC(P->d_colmax, P->K);
     }
     if (P->proj_tc) WDD_ALLOC(P->d_bimg, proj_tc_bimg_halves(P->Nx, P->Lx));
+    if (p.accum_mode == WDD_ACCUM_SEPARABLE) {
+        const int R = rows_slots(P->Sy, P->depth_pad);
+        WDD_ALLOC(P->d_G, (size_t)R * P->Sx * P->K);
+        WDD_ALLOC(P->d_slotrow, R);
+        WDD_ALLOC(P->d_slotfirst, R);
+        WDD_ALLOC(P->d_slotlast, R);
+        WDD_ALLOC(P->d_frameslot, P->depth_pad);
+        WDD_ALLOC(P->d_nslots, 1);
+    }
 #undef WDD_ALLOC
 
     cudaStream_t s0 = nullptr;
@@ -741,7 +760,7 @@ wdd_status wdd_plan_get_info(const wdd_plan* P, wdd_plan_info* out) {
     out->staged = P->staged;
     out->finished = P->finished ? 1 : 0;
     out->proj_tensor = P->proj_tc;
-    out->reserved0 = 0;
+    out->accum_mode = P->p.accum_mode;
     return WDD_OK;
 }
 

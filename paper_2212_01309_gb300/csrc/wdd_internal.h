@@ -89,6 +89,13 @@ struct wdd_plan {
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
+    // SEPARABLE accumulation: per-flush row slots and row DFTs
+    float2* d_G = nullptr;          // [slots][Sx][K]
+    int32_t* d_slotrow = nullptr;   // [slots] scan row of each slot
+    int32_t* d_slotfirst = nullptr; // [slots] first / last staged frame of each slot
+    int32_t* d_slotlast = nullptr;
+    int32_t* d_frameslot = nullptr; // [depth_pad] slot of each staged frame
+    int32_t* d_nslots = nullptr;    // [1] slots in use
     int proj_tc = 0;               // 1: projection on the tensor cores
     int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
     int segment = 1024;            // split path: frames per tensor-core accumulation launch
@@ -161,6 +168,11 @@ cudaError_t launch_build_bimg(const wdd_plan* P, uint16_t* img, cudaStream_t st)
 cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, int n, bool overlap,
                               const IndexBlock& idx, float* c_out, int32_t* idx_out,
                               cudaStream_t st);
+// Row-factorised accumulation (SEPARABLE mode).
+int rows_slots(int Sy, int depth_pad);   // slots a flush of depth_pad frames can need
+cudaError_t prepare_rows_kernels();
+cudaError_t launch_accumulate_rows(const wdd_plan* P, const float* c, const int32_t* idx, int n,
+                                   cudaStream_t st);
 cudaError_t launch_accumulate_fp32(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                    cudaStream_t st);
 // Device-side waits give up after this long and report WDD_ERR_TIMEOUT.

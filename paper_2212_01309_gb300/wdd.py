@@ -22,6 +22,7 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_SCAN_INDEX, ERR_STATE, ERR
 BASIS = {"fourier_full": 0, "hg_tensor": 1, "hg_energy": 2}
 PRECISION = {"fp32": 0, "split": 1}
 FRAME_DTYPE = {"u16": 0, "f32": 1, "f64": 2}
+ACCUM_MODE = {"direct": 0, "separable": 1}
 ARRAY = {"weights": 0, "chi": 1, "accum": 2, "coeff": 3, "spectrum": 4, "basis_y": 5,
          "basis_x": 6, "mask": 7, "coeff_index": 8}
 
@@ -55,6 +56,7 @@ class Params(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_int64),
         ("overlap_pushes", ctypes.c_int32),
         ("accum_segment", ctypes.c_int32),
+        ("accum_mode", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -72,7 +74,7 @@ class PlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_int64), ("frames_seen", ctypes.c_int64),
         ("positions_covered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("staged", ctypes.c_int32), ("finished", ctypes.c_int32),
-        ("proj_tensor", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("proj_tensor", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
     ]
 
 
@@ -145,7 +147,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 precision="fp32", frame_dtype="f32", max_batch=256, accum_depth=0,
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
                 hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False,
-                accum_segment=0) -> Params:
+                accum_segment=0, accum_mode="direct") -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -162,6 +164,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.proj_cluster = proj_cluster
     p.overlap_pushes = 1 if overlap_pushes else 0
     p.accum_segment = accum_segment
+    p.accum_mode = ACCUM_MODE[accum_mode] if isinstance(accum_mode, str) else int(accum_mode)
     return p
 
 
