@@ -35,7 +35,8 @@ WORKLOAD = "c2"
 METRIC = "live WDD frames/s and p99 frame latency vs plain FP32 path; % tensor peak"
 UNIT = "frames/s"
 LATENCY_SNAPSHOT_EVERY = 1024
-ACCUM_DEPTH = 4096          # frames staged per tensor-core accumulation on the optimised path
+ACCUM_DEPTH = 4096     # frames staged per tensor-core accumulation on the optimised path
+COALESCE = 1024        # pushes gathered into projection launches of up to 1024 frames
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
@@ -330,17 +331,18 @@ def main(argv=None) -> int:
                 raise
         path = "split" if split_ok else "fp32"
 
-    def mk(precision, depth, overlap, mode="direct"):
+    def mk(precision, depth, overlap, mode="direct", coalesce=0):
         return wdd.Plan(wdd.params_from_acquisition(
             acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"],
             precision=precision, max_batch=B, accum_depth=depth, overlap_pushes=overlap,
-            accum_mode=mode))
+            accum_mode=mode, coalesce_frames=coalesce))
 
     # the plain path: FP32 SIMT, every push accumulated at once, eager launches
     plain = mk("fp32", 0, False)
     # the optimised path: tensor-core split accumulation over ACCUM_DEPTH staged frames,
-    # consecutive pushes overlapped (the frames are device-resident before the step starts)
-    opt = mk(path, ACCUM_DEPTH, True)
+    # consecutive pushes overlapped and gathered into 1024-frame projection launches (the
+    # frames are resident for the whole step)
+    opt = mk(path, ACCUM_DEPTH, True, coalesce=COALESCE)
 
     def step(plan, src):
         plan.reset(stream=stream)
@@ -403,7 +405,7 @@ def main(argv=None) -> int:
         st = opt.stage_times()
 
         # ---- variant: scan-row factorised accumulation (not the paper's form), same step ----
-        sep = mk(path, ACCUM_DEPTH, True, mode="separable")
+        sep = mk(path, ACCUM_DEPTH, True, mode="separable", coalesce=COALESCE)
         for _ in range(args.warmup):
             step(sep, d_frames)
         sgraph = torch.cuda.CUDAGraph()
@@ -527,7 +529,7 @@ def main(argv=None) -> int:
             "config": {"workload": "128x128 scan, 128x128 f32 detector (Poisson 1e4 e-/frame), "
                                    "Hermite-Gauss K=64, 64-frame pushes, snapshot per step",
                        "name": WORKLOAD, "path": path, "accum_depth": ACCUM_DEPTH,
-                       "overlap_pushes": True,
+                       "overlap_pushes": True, "coalesce_frames": COALESCE,
                        "cuda_graph": True,
                        "l2": "inputs larger than L2 (1.07 GB of frames per step)"},
             "baseline_fp32_plain": {"value": job_throughput(S, world, ms_plain), "unit": UNIT,

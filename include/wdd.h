@@ -92,7 +92,8 @@ typedef struct {
     int32_t basis;            /* wdd_basis                                                     */
     int32_t precision;        /* wdd_precision                                                 */
     int32_t frame_dtype;      /* wdd_frame_dtype                                               */
-    int32_t max_batch;        /* most frames per internal launch; larger pushes are split      */
+    int32_t max_batch;        /* most frames per internal launch (at most 1024); larger pushes
+                                 are split                                                     */
     int32_t accum_depth;      /* frames staged before the phase accumulation runs; 0 = every
                                  push is accumulated at once (the plain path)                  */
     double det_center_y;      /* detector zero-frequency pixel; negative = det_y / 2 (integer) */
@@ -113,7 +114,13 @@ typedef struct {
                                  3.8e-6 at 4096 on a 128x128 scan); longer segments run faster.
                                  0 = 1024. */
     int32_t accum_mode;       /* wdd_accum_mode: how staged frames are added into H            */
-    int32_t reserved2;
+    int32_t coalesce_frames;  /* tensor-core projection: device or pinned-host pushes are gathered
+                                 until this many frames are pending (at most 1024, from at most 16
+                                 pushes) and projected in one launch.  The caller must then keep a
+                                 push's frames unchanged until the plan's next wdd_flush,
+                                 wdd_snapshot, wdd_finalize, wdd_reset or wdd_set_stream, or until
+                                 wdd_plan_info reports pending == 0.  0 = every push is projected
+                                 when it is made. */
 } wdd_params;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
@@ -205,6 +212,8 @@ typedef struct {
                                 real basis, uint16/float32 frames, det_x a multiple of 16);
                                 0: on the SIMT cores in FP32                                  */
     int32_t accum_mode;      /* wdd_accum_mode of the plan                                   */
+    int32_t pending;         /* frames gathered for a projection launch (coalesce_frames)    */
+    int32_t reserved0;
 } wdd_plan_info;
 
 /* Reports the plan's derived constants and counters (host-side, no GPU work). */

@@ -145,7 +145,8 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += 4LL * P->depth * P->K + 4LL * P->depth;            // staging
     b += 16LL * P->S;                                       // spectrum + DFT scratch
     b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
-    if (P->proj_tc) b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx);   // basis image
+    if (P->proj_tc)                                                          // basis image, By
+        b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx) + 4LL * ((P->Ny * P->Ly + 3) / 4 * 4);
     if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) {                            // row slots, G
         const int64_t R = rows_slots(P->Sy, P->depth_pad);
         b += 8LL * R * P->Sx * P->K + 12LL * R + 4LL * P->depth_pad + 4;
@@ -191,7 +192,30 @@ cudaError_t staged_launch(wdd_plan* P, int stage, int count, F&& launch) {
     return cudaSuccess;
 }
 
+// Projects the pushes gathered for one launch (coalesce_frames), on the plan's stream.
+wdd_status launch_pending(wdd_plan* P) {
+    wdd::PendingLaunch& q = P->pend;
+    if (q.n == 0) return WDD_OK;
+    q.segs.first[q.segs.nseg] = q.n;
+    float* c_out = P->d_cstage + (size_t)q.slot0 * P->K;
+    int32_t* i_out = P->d_idxstage + q.slot0;
+    cudaError_t e = staged_launch(P, WDD_STAGE_PROJECT, 1, [&] {
+        return launch_project_tc(P, q.segs, P->p.frame_dtype, q.n, P->p.overlap_pushes != 0, q.ids,
+                                 c_out, i_out, P->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "projection");
+    P->last_coeff_off = q.slot0;
+    P->last_coeff_n = q.n;
+    q.n = 0;
+    q.segs.nseg = 0;
+    return WDD_OK;
+}
+
 wdd_status flush(wdd_plan* P) {
+    {
+        wdd_status ls = launch_pending(P);
+        if (ls != WDD_OK) return ls;
+    }
     if (P->staged == 0) return WDD_OK;
     const bool rows = P->p.accum_mode == WDD_ACCUM_SEPARABLE;
     const int count = rows ? 3
@@ -219,6 +243,9 @@ wdd_status acquire_slot(wdd_plan* P, wdd::RingSlot** out) {
 // Makes `st` the plan's stream, ordering it after everything enqueued on the previous one.
 wdd_status switch_stream(wdd_plan* P, cudaStream_t st) {
     if (P->stream_set && st != P->stream) {
+        // gathered pushes belong to the old stream
+        wdd_status ls = launch_pending(P);
+        if (ls != WDD_OK) return ls;
         WDD_CUDA(cudaEventRecord(P->handoff, P->stream));
         WDD_CUDA(cudaStreamWaitEvent(st, P->handoff, 0));
     }
@@ -314,6 +341,8 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         return fail(WDD_ERR_INVALID_ARG, "accum_segment must be in [0, 8192]");
     if (p.accum_mode != WDD_ACCUM_DIRECT && p.accum_mode != WDD_ACCUM_SEPARABLE)
         return fail(WDD_ERR_INVALID_ARG, "unknown accumulation mode");
+    if (p.coalesce_frames < 0 || p.coalesce_frames > kLaunchFrames)
+        return fail(WDD_ERR_INVALID_ARG, "coalesce_frames must be in [0, 1024]");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -498,7 +527,10 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         WDD_ALLOC(P->d_scale_inv, Kp);
         WDD_ALLOC(P->d_colmax, P->K);
     }
-    if (P->proj_tc) WDD_ALLOC(P->d_bimg, proj_tc_bimg_halves(P->Nx, P->Lx));
+    if (P->proj_tc) {
+        WDD_ALLOC(P->d_bimg, proj_tc_bimg_halves(P->Nx, P->Lx));
+        WDD_ALLOC(P->d_Byre, ((size_t)P->Ny * P->Ly + 3) / 4 * 4);
+    }
     if (p.accum_mode == WDD_ACCUM_SEPARABLE) {
         const int R = rows_slots(P->Sy, P->depth_pad);
         WDD_ALLOC(P->d_G, (size_t)R * P->Sx * P->K);
@@ -537,6 +569,11 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         for (size_t i = 0; i < bx.size(); ++i) fx[i] = make_float2((float)bx[i].x, (float)bx[i].y);
         if ((e = cudaMemcpy(P->d_By32, fy.data(), 8 * fy.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
         if ((e = cudaMemcpy(P->d_Bx32, fx.data(), 8 * fx.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+        if (P->d_Byre) {
+            std::vector<float> re((by.size() + 3) / 4 * 4, 0.f);
+            for (size_t i = 0; i < by.size(); ++i) re[i] = (float)by[i].x;
+            if ((e = cudaMemcpy(P->d_Byre, re.data(), 4 * re.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+        }
     }
 
     // ---- Algorithm 1: chi_v, eps_eff, Wiener weights ------------------------------------
@@ -657,7 +694,46 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
         wdd_status ss = switch_stream(P, st);
         if (ss != WDD_OK) return ss;
     }
-    for (int64_t off = 0; off < n; off += P->chunk) {
+    const bool coalesce = P->p.coalesce_frames > 0 && P->proj_tc && !pageable &&
+                          (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    if (coalesce) {
+        // gather into the pending launch (at most kLaunchFrames frames from kMaxSegs pushes,
+        // and no more than the staging depth)
+        wdd::PendingLaunch& q = P->pend;
+        const int cap = std::min(kLaunchFrames, P->depth);
+        for (int64_t off = 0; off < n;) {
+            if (q.n == cap || q.segs.nseg == kMaxSegs) {
+                wdd_status ls = launch_pending(P);
+                if (ls != WDD_OK) return ls;
+            }
+            int nb = (int)std::min<int64_t>(cap - q.n, n - off);
+            if (P->staged + nb > P->depth) {
+                wdd_status fs = flush(P);   // launches the pending frames first
+                if (fs != WDD_OK) return fs;
+                nb = (int)std::min<int64_t>(cap, n - off);
+            }
+            if (q.n == 0) q.slot0 = P->staged;
+            q.segs.ptr[q.segs.nseg] = src + fbytes * off;
+            q.segs.first[q.segs.nseg] = q.n;
+            ++q.segs.nseg;
+            std::memcpy(q.ids.s + q.n, scan_idx + off, sizeof(int32_t) * nb);
+            q.n += nb;
+            P->staged += nb;
+            off += nb;
+        }
+        if (q.n >= P->p.coalesce_frames) {
+            wdd_status ls = launch_pending(P);
+            if (ls != WDD_OK) return ls;
+        }
+        if (P->p.accum_depth == 0) {
+            wdd_status fs = flush(P);
+            if (fs != WDD_OK) return fs;
+        }
+    } else {
+        wdd_status ls = launch_pending(P);   // keep launches in push order
+        if (ls != WDD_OK) return ls;
+    }
+    for (int64_t off = 0; off < n && !coalesce; off += P->chunk) {
         int nb = (int)std::min<int64_t>(P->chunk, n - off);
         bool flushed = false;
         if (P->staged + nb > P->depth) {
@@ -687,9 +763,15 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
             // after all earlier work on the stream), or when the caller allowed overlap across
             // pushes
             const bool overlap = off > 0 || flushed || P->p.overlap_pushes != 0;
-            if (P->proj_tc && (reinterpret_cast<uintptr_t>(fsrc) & 15u) == 0)
-                return launch_project_tc(P, fsrc, P->p.frame_dtype, nb, overlap, ids, c_out, i_out,
+            if (P->proj_tc && (reinterpret_cast<uintptr_t>(fsrc) & 15u) == 0) {
+                wdd::FrameSegs one{};
+                one.ptr[0] = fsrc;
+                one.first[0] = 0;
+                one.first[1] = nb;
+                one.nseg = 1;
+                return launch_project_tc(P, one, P->p.frame_dtype, nb, overlap, ids, c_out, i_out,
                                          st);
+            }
             return launch_project(P, fsrc, P->p.frame_dtype, nb, device_src, overlap, ids, c_out,
                                   i_out, st);
         });
@@ -736,6 +818,8 @@ wdd_status wdd_reset(wdd_plan* P) {
     WDD_CUDA(cudaMemsetAsync(P->d_H, 0, 8 * (size_t)P->S * P->K, P->stream));
     if (P->d_colmax) WDD_CUDA(cudaMemsetAsync(P->d_colmax, 0, 4 * (size_t)P->K, P->stream));
     P->staged = 0;
+    P->pend.n = 0;             // gathered pushes are dropped with the staged frames
+    P->pend.segs.nseg = 0;
     P->frames_seen = 0;
     P->covered = 0;
     P->finished = false;
@@ -761,6 +845,8 @@ wdd_status wdd_plan_get_info(const wdd_plan* P, wdd_plan_info* out) {
     out->finished = P->finished ? 1 : 0;
     out->proj_tensor = P->proj_tc;
     out->accum_mode = P->p.accum_mode;
+    out->pending = P->pend.n;
+    out->reserved0 = 0;
     return WDD_OK;
 }
 

@@ -31,9 +31,24 @@ struct ProjGeom {
     int use_tma;                // 1: device frames copied by cp.async.bulk
 };
 // Frames per projection launch; their scan indices travel as a kernel parameter block.
-constexpr int kLaunchFrames = 256;
+constexpr int kLaunchFrames = 1024;
 struct IndexBlock {
     int32_t s[kLaunchFrames];
+};
+// Frames of one tensor-core projection launch, possibly from several pushes: CTA b projects
+// frame b - first[j] of segment j, where first[j] <= b < first[j + 1].
+constexpr int kMaxSegs = 16;
+struct FrameSegs {
+    const void* ptr[kMaxSegs];
+    int32_t first[kMaxSegs + 1];
+    int32_t nseg;
+};
+// Pushes gathered for one launch (wdd_params.coalesce_frames).
+struct PendingLaunch {
+    FrameSegs segs{};
+    IndexBlock ids{};
+    int n = 0;          // frames gathered
+    int slot0 = 0;      // staging slot of the first of them
 };
 // Pinned ring slots for host-side staging of pageable frames.
 constexpr int kRingSlots = 4;
@@ -89,6 +104,7 @@ struct wdd_plan {
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
+    float* d_Byre = nullptr;       // tensor-core projection: real parts of By, [Ny * Ly] padded to 4
     // SEPARABLE accumulation: per-flush row slots and row DFTs
     float2* d_G = nullptr;          // [slots][Sx][K]
     int32_t* d_slotrow = nullptr;   // [slots] scan row of each slot
@@ -99,6 +115,7 @@ struct wdd_plan {
     int proj_tc = 0;               // 1: projection on the tensor cores
     int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
     int segment = 1024;            // split path: frames per tensor-core accumulation launch
+    wdd::PendingLaunch pend;       // pushes gathered for one projection launch
 
     // host bookkeeping (exact)
     std::vector<uint32_t> hits;
@@ -165,8 +182,8 @@ size_t proj_tc_smem_bytes(int Ny, int Nx, int Ly, int Lx, int K);
 size_t proj_tc_bimg_halves(int Nx, int Lx);
 cudaError_t prepare_project_tc_kernels();
 cudaError_t launch_build_bimg(const wdd_plan* P, uint16_t* img, cudaStream_t st);
-cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, int n, bool overlap,
-                              const IndexBlock& idx, float* c_out, int32_t* idx_out,
+cudaError_t launch_project_tc(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
+                              bool overlap, const IndexBlock& idx, float* c_out, int32_t* idx_out,
                               cudaStream_t st);
 // Row-factorised accumulation (SEPARABLE mode).
 int rows_slots(int Sy, int depth_pad);   // slots a flush of depth_pad frames can need

@@ -15,11 +15,13 @@
 //
 // One CTA per frame.  The frame is read in (128-row tile, 32-column chunk) items with 16-byte
 // loads, coalesced along rows (frames in pinned host memory are read over the host link by the
-// same loads); the loads of the next kPD items are in flight while one item is converted.  The
-// threads split an item into its FP16 parts and store them in the UMMA no-swizzle K-major
-// layout, and one thread issues the MMAs.  After each tile the accumulator rows (one TMEM lane
-// per detector row) are read back into a shared-memory T tile.  Several CTAs share an SM, so one
-// CTA's loads overlap another's conversion.
+// same loads); the next item's loads are in flight while one item is converted.  The threads
+// split an item into its FP16 parts and store them in one of two A buffers in the UMMA
+// no-swizzle K-major layout, and one thread issues the MMAs, so converting an item overlaps the
+// MMAs of the previous one.  The basis image and By arrive by TMA bulk copies while the first
+// item is converted.  After each tile the accumulator rows (one TMEM lane per detector row) are
+// read back, the hi and lo column groups added in registers, into a shared-memory T tile.
+// Several CTAs share an SM, so one CTA's loads overlap another's conversion.
 //
 // Launch ordering is the same as the SIMT projection's (programmatic dependent launch, outputs
 // written after griddepcontrol.wait).  The CTA allocates its tensor memory before it lets the
@@ -43,11 +45,10 @@ constexpr int kU = kTK / 16;      // (8-row group, 32-column quarter) units per 
 constexpr int kAHalfBytes = kTM * kTK * 2;   // one FP16 part of a chunk
 
 struct PtcArgs {
-    const void* frames;
     int Ny, Nx, Ly, Lx, K, Np, SP, tmem_cols;
     float scale, inv_scale;
     const uint16_t* bimg;     // B operand image (see build_bimg_kernel)
-    const float2* By;         // [Ny][Ly] (real part used)
+    const float* By;          // [Ny * Ly rounded up to 4] real parts of the row basis
     const int2* ktab;         // [K] (ly * Lx + lx, 0)
     float* c_out;             // [n][K]
     int32_t* idx_out;         // [n]
@@ -60,19 +61,21 @@ struct PtcLayout {
     size_t b, a, by, t, red, bar, slot, total;
 };
 
+__host__ __device__ inline size_t by_floats(int Ny, int Ly) { return ((size_t)Ny * Ly + 3) / 4 * 4; }
+
 __host__ __device__ inline PtcLayout ptc_layout(int Ny, int Nx, int Ly, int Lx, int K, int Np,
                                                 int SP) {
     PtcLayout L;
     L.b = 0;
     L.a = (L.b + (size_t)Np * Nx * 2 + 127) & ~size_t(127);
-    // A chunk (hi, lo), also holding the padded accumulator rows of a finished tile
-    const size_t a_bytes = 2 * (size_t)kAHalfBytes > (size_t)kTM * (Np + 1) * 4
-                               ? 2 * (size_t)kAHalfBytes : (size_t)kTM * (Np + 1) * 4;
+    // two A buffers (hi, lo), also holding the padded accumulator rows of a finished tile
+    const size_t a_bytes = 4 * (size_t)kAHalfBytes > (size_t)kTM * (Np + 1) * 4
+                               ? 4 * (size_t)kAHalfBytes : (size_t)kTM * (Np + 1) * 4;
     L.by = L.a + ((a_bytes + 15) & ~size_t(15));
-    L.t = (L.by + 4 * (size_t)Ny * Ly + 15) & ~size_t(15);
+    L.t = (L.by + 4 * by_floats(Ny, Ly) + 15) & ~size_t(15);
     L.red = (L.t + 4 * (size_t)Ny * Lx + 15) & ~size_t(15);
-    L.bar = (L.red + 4 * (size_t)SP * K + 15) & ~size_t(15);
-    L.slot = L.bar + 8;
+    L.bar = (L.red + 4 * (size_t)SP * K + 15) & ~size_t(15);   // MMA buffer 0, 1; basis copy
+    L.slot = L.bar + 24;
     L.total = L.slot + 8;
     return L;
 }
@@ -152,9 +155,6 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Items whose loads are in flight while one is converted.
-constexpr int kPD = 1;
-
 // Loads this thread's part of item `it` = (tile it / chunks, chunk it % chunks): for unit
 // v = warp + 8 u, row 8 (v % 16) + r of the tile and columns 32 (v / 16) + 8 q .. + 7 of the
 // chunk; zeros outside the frame.
@@ -177,38 +177,59 @@ __device__ __forceinline__ void load_item(const FT* frame, int it, int n_items, 
     }
 }
 
+// T[row][0 .. LX) = (D[row][n] + D[row][LX + n]) * inv for n < LX from the thread's TMEM lane
+// (columns 0 .. LX - 1 hold the Bx_hi products, LX .. 2 LX - 1 the Bx_lo ones).
+template <int LX>
+__device__ __forceinline__ void tile_rows_direct(uint32_t taddr, float inv, float* trow, bool ok) {
+    float d[2 * LX > 16 ? 2 * LX : 16];
+#pragma unroll
+    for (int c0 = 0; c0 < 2 * LX; c0 += 16) tmem_ld_x16(taddr + (uint32_t)c0, d + c0);
+    if (ok) {
+#pragma unroll
+        for (int n = 0; n < LX; n += 4)
+            *reinterpret_cast<float4*>(trow + n) =
+                make_float4((d[n] + d[LX + n]) * inv, (d[n + 1] + d[LX + n + 1]) * inv,
+                            (d[n + 2] + d[LX + n + 2]) * inv, (d[n + 3] + d[LX + n + 3]) * inv);
+    }
+}
+
 template <typename FT>
 __global__ void __launch_bounds__(kThreads, 3)
-project_tc_kernel(const PtcArgs a, const IndexBlock ids) {
+project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
     extern __shared__ __align__(128) uint8_t sm[];
     const int tiles = (a.Ny + kTM - 1) / kTM;
     const PtcLayout L = ptc_layout(a.Ny, a.Nx, a.Ly, a.Lx, a.K, a.Np, a.SP);
     uint8_t* sB = sm + L.b;
-    uint8_t* sA = sm + L.a;                 // [hi | lo], each [16 row groups][4 K-chunks][8][8]
+    uint8_t* sA = sm + L.a;                 // 2 x [hi | lo], each [16 row groups][4 K-chunks][8][8]
     float* sBy = reinterpret_cast<float*>(sm + L.by);
     float* sT = reinterpret_cast<float*>(sm + L.t);
     float* red = reinterpret_cast<float*>(sm + L.red);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);   // MMA completion
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L.bar);   // [2] MMAs of A buffer 0 / 1
+    uint64_t* bload = mbar + 2;                                 // basis image and By copies
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + L.slot);
     __shared__ int s_fail;
 
     const int b = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const FT* frame = static_cast<const FT*>(a.frames) + (size_t)b * a.Ny * a.Nx;
+    int sg = 0;
+    while (sg + 1 < segs.nseg && b >= segs.first[sg + 1]) ++sg;
+    const FT* frame = static_cast<const FT*>(segs.ptr[sg]) + (size_t)(b - segs.first[sg]) * a.Ny * a.Nx;
     // lane -> (row r of an 8-row group, 8-column K-chunk q of a 32-column quarter); warp w
     // converts the units w, w + 8, ... (unit v: row group v % 16, quarter v / 16)
     const int r = lane & 7, q = lane >> 3;
     const int chunks = a.Nx / kTK + (a.Nx % kTK ? 1 : 0);
     const int n_items = tiles * chunks;     // (tile, chunk) items in order
-    // raw values of the items in flight (register ring, compile-time slots)
-    float x[kPD][kU][8];
-    // the first items' loads go out before anything else
-#pragma unroll
-    for (int j = 0; j < kPD; ++j) load_item(frame, j, n_items, chunks, a.Ny, a.Nx, warp, r, q, x[j]);
+    float x[kU][8];                         // raw values of the item in flight
+    // the first item's loads go out before anything else
+    load_item(frame, 0, n_items, chunks, a.Ny, a.Nx, warp, r, q, x);
 
+    const unsigned b_bytes = (unsigned)(a.Np * a.Nx * 2);
+    const unsigned by_bytes = (unsigned)(4 * by_floats(a.Ny, a.Ly));
     if (threadIdx.x == 0) {
         s_fail = 0;
-        mbar_init(bar, 1);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init(bload, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -223,86 +244,110 @@ project_tc_kernel(const PtcArgs a, const IndexBlock ids) {
     const uint32_t tmem = *slot;
     // the next launch may start now: this CTA already holds its tensor memory
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
-    // B operand image and By into shared memory
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(a.bimg);
-        uint4* dst = reinterpret_cast<uint4*>(sB);
-        const int n16 = a.Np * a.Nx / 8;
-        for (int t = threadIdx.x; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
-        for (int t = threadIdx.x; t < a.Ny * a.Ly; t += blockDim.x) sBy[t] = a.By[t].x;
+    // basis image (B operand) and By: bulk copies, complete before the first MMA / contraction
+    if (threadIdx.x == 0) {
+        mbar_arrive_tx(bload, b_bytes + by_bytes);
+        tma_load_1d(sB, a.bimg, b_bytes, bload);
+        tma_load_1d(sBy, a.By, by_bytes, bload);
     }
+    // this thread's first coefficient of the second contraction, fetched early
+    const int m_first = threadIdx.x < a.K * a.SP ? __ldg(&a.ktab[threadIdx.x % a.K].x) : 0;
 
     const uint32_t idesc = idesc_f16(kTM, a.Np);
     const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
     const uint32_t sboB = (uint32_t)(a.Nx / 8) * 128u;
-    unsigned waits = 0, commits = 0;
-    bool range_bad = false;
+    bool range_bad = false, basis_ready = false;
+    int issued = 0, done = 0;   // items whose MMAs were issued / are known complete
 
-    for (int it0 = 0; it0 < n_items && !s_fail; it0 += kPD) {
-#pragma unroll
-        for (int j = 0; j < kPD; ++j) {
-            const int it = it0 + j;
-            if (it >= n_items || s_fail) break;
-            const int mt = it / chunks, kc = it % chunks;
-            const int w = min(kTK, a.Nx - kc * kTK);
-            // the A buffer is free once the previous chunk's MMAs have completed
-            if (commits > waits && threadIdx.x == 0 && !mbar_wait(bar, waits & 1u, a.wait_ns)) {
+    for (int it = 0; it < n_items; ++it) {
+        const int mt = it / chunks, kc = it % chunks;
+        const int w = min(kTK, a.Nx - kc * kTK);
+        const int ab = it & 1;
+        uint8_t* sAb = sA + (size_t)ab * 2 * kAHalfBytes;
+        // buffer ab is free once the MMAs of item it - 2 have completed (they complete in order)
+        if (it >= 2 && done < it - 1) {
+            if (threadIdx.x == 0 &&
+                !mbar_wait(&mbar[ab], (unsigned)((it - 2) >> 1) & 1u, a.wait_ns)) {
                 atomicExch(a.status, 8u);
                 s_fail = 1;
             }
-            __syncthreads();
-            if (s_fail) break;
-            waits = commits;
-            // split and store in the UMMA layout: offset (g * kKC + K-chunk) * 128 + r * 16
+            done = it - 1;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        // split and store in the UMMA layout: offset (g * kKC + K-chunk) * 128 + r * 16
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int v = warp + 8 * u;
-                const int kcl = 4 * (v >> 4) + q;     // K-chunk within the chunk
-                if (8 * kcl < w) {
-                    float y[8];
+        for (int u = 0; u < kU; ++u) {
+            const int v = warp + 8 * u;
+            const int kcl = 4 * (v >> 4) + q;     // K-chunk within the chunk
+            if (8 * kcl < w) {
+                float y[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        y[e] = x[j][u][e] * a.scale;
-                        range_bad |= !(fabsf(y[e]) <= 65504.f);
-                    }
-                    uint4 hi, lo;
-                    split8(y, hi, lo);
-                    const int off = ((v & 15) * kKC + kcl) * 128 + r * 16;
-                    *reinterpret_cast<uint4*>(sA + off) = hi;
-                    *reinterpret_cast<uint4*>(sA + kAHalfBytes + off) = lo;
+                for (int e = 0; e < 8; ++e) {
+                    y[e] = x[u][e] * a.scale;
+                    range_bad |= !(fabsf(y[e]) <= 65504.f);
                 }
+                uint4 hi, lo;
+                split8(y, hi, lo);
+                const int off = ((v & 15) * kKC + kcl) * 128 + r * 16;
+                *reinterpret_cast<uint4*>(sAb + off) = hi;
+                *reinterpret_cast<uint4*>(sAb + kAHalfBytes + off) = lo;
             }
-            // this slot's values are used: load the item kPD ahead into it
-            load_item(frame, it + kPD, n_items, chunks, a.Ny, a.Nx, warp, r, q, x[j]);
-            fence_async_smem();
-            __syncthreads();
-            // one thread issues the MMAs of this chunk: D[row][n] += A_hi B^T + A_lo B^T
-            if (threadIdx.x == 0) {
+        }
+        // the next item's loads
+        load_item(frame, it + 1, n_items, chunks, a.Ny, a.Nx, warp, r, q, x);
+        fence_async_smem();
+        __syncthreads();
+        // one thread issues the MMAs of this chunk: D[row][n] += A_hi B^T + A_lo B^T
+        if (threadIdx.x == 0) {
+            if (!basis_ready) {
+                if (!mbar_wait(bload, 0, a.wait_ns)) {
+                    atomicExch(a.status, 8u);
+                    s_fail = 1;
+                }
+                basis_ready = true;
+            }
+            if (!s_fail) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sAb_u = sA_u + (uint32_t)(ab * 2 * kAHalfBytes);
                 for (int ks = 0; ks < w / 16; ++ks) {
-                    const uint64_t ah = desc_nosw(sA_u + (uint32_t)ks * 256u, 128, kKC * 128);
+                    const uint64_t ah = desc_nosw(sAb_u + (uint32_t)ks * 256u, 128, kKC * 128);
                     const uint64_t al =
-                        desc_nosw(sA_u + kAHalfBytes + (uint32_t)ks * 256u, 128, kKC * 128);
+                        desc_nosw(sAb_u + kAHalfBytes + (uint32_t)ks * 256u, 128, kKC * 128);
                     const uint64_t bd =
                         desc_nosw(sB_u + (uint32_t)(kc * kKC + 2 * ks) * 128u, 128, sboB);
                     umma_f16(tmem, ah, bd, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
                     umma_f16(tmem, al, bd, idesc, 1u);
                 }
-                umma_commit(bar);
+                umma_commit(&mbar[ab]);
             }
-            ++commits;
-            if (kc + 1 < chunks) continue;
-            // tile epilogue: TMEM lane = detector row; T[row][lx] = (D[lx] + D[Lx + lx]) / s
-            if (threadIdx.x == 0 && !mbar_wait(bar, waits & 1u, a.wait_ns)) {
-                atomicExch(a.status, 8u);
-                s_fail = 1;
+        }
+        issued = it + 1;
+        if (kc + 1 < chunks) continue;
+        // tile epilogue: wait for this tile's MMAs; TMEM lane = detector row
+        if (threadIdx.x == 0 && !s_fail && !mbar_wait(&mbar[ab], (unsigned)(it >> 1) & 1u, a.wait_ns)) {
+            atomicExch(a.status, 8u);
+            s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        done = it + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (a.Lx == 8 || a.Lx == 16) {
+            // T[row][lx] = (D[lx] + D[Lx + lx]) / s straight from the thread's TMEM lane
+            if (warp < 4) {
+                const int row = mt * kTM + 32 * warp + lane;
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+                float* trow = sT + (size_t)row * a.Lx;
+                if (a.Lx == 8)
+                    tile_rows_direct<8>(taddr, a.inv_scale, trow, row < a.Ny);
+                else
+                    tile_rows_direct<16>(taddr, a.inv_scale, trow, row < a.Ny);
             }
-            __syncthreads();
-            if (s_fail) break;
-            waits = commits;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // raw accumulator rows -> the idle A buffer (row stride Np + 1: conflict-free stores)
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();   // TMEM is read: the next tile's first MMA may overwrite it
+        } else {
+            // raw accumulator rows -> the idle A buffers (row stride Np + 1: conflict-free)
             float* sD = reinterpret_cast<float*>(sA);
             const int ldD = a.Np + 1;
             if (warp < 4) {
@@ -325,7 +370,7 @@ project_tc_kernel(const PtcArgs a, const IndexBlock ids) {
                     sT[(size_t)row * a.Lx + lx] =
                         (sD[(size_t)rl * ldD + lx] + sD[(size_t)rl * ldD + a.Lx + lx]) * a.inv_scale;
             }
-            __syncthreads();   // the A buffer is free again
+            __syncthreads();   // the A buffers are free again
         }
     }
     if (range_bad) atomicExch(a.status, 9u);
@@ -336,7 +381,7 @@ project_tc_kernel(const PtcArgs a, const IndexBlock ids) {
     if (!failed) {
         for (int t = threadIdx.x; t < a.K * a.SP; t += blockDim.x) {
             const int k = t % a.K, sl = t / a.K;
-            const int m = __ldg(&a.ktab[k].x);
+            const int m = (t == threadIdx.x) ? m_first : __ldg(&a.ktab[k].x);
             const int ly = m / a.Lx, lx = m % a.Lx;
             float acc = 0.f;
             for (int i = sl; i < a.Ny; i += a.SP)
@@ -357,8 +402,9 @@ project_tc_kernel(const PtcArgs a, const IndexBlock ids) {
         }
     }
     if (failed && threadIdx.x == 0) {
-        // before the tensor memory goes: one more bounded wait for an outstanding MMA commit
-        if (commits > waits) mbar_wait(bar, waits & 1u, a.wait_ns);
+        // before the tensor and shared memory go: bounded waits for MMAs and copies in flight
+        for (int j = done; j < issued; ++j) mbar_wait(&mbar[j & 1], (unsigned)(j >> 1) & 1u, a.wait_ns);
+        if (!basis_ready) mbar_wait(bload, 0, a.wait_ns);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -422,13 +468,12 @@ cudaError_t prepare_project_tc_kernels() {
     return e;
 }
 
-cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, int n, bool overlap,
-                              const IndexBlock& ids, float* c_out, int32_t* idx_out,
+cudaError_t launch_project_tc(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
+                              bool overlap, const IndexBlock& ids, float* c_out, int32_t* idx_out,
                               cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (n > kLaunchFrames) return cudaErrorInvalidValue;
     PtcArgs a;
-    a.frames = frames;
     a.Ny = P->Ny;
     a.Nx = P->Nx;
     a.Ly = P->Ly;
@@ -440,7 +485,7 @@ cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, 
     a.scale = dtype == WDD_FRAME_U16 ? 0.5f : 1.0f;
     a.inv_scale = dtype == WDD_FRAME_U16 ? 2.0f : 1.0f;
     a.bimg = P->d_bimg;
-    a.By = P->d_By32;
+    a.By = P->d_Byre;
     a.ktab = P->d_ktab;
     a.c_out = c_out;
     a.idx_out = idx_out;
@@ -457,8 +502,9 @@ cudaError_t launch_project_tc(const wdd_plan* P, const void* frames, int dtype, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = overlap ? 1 : 0;
-    if (dtype == WDD_FRAME_U16) return cudaLaunchKernelEx(&cfg, project_tc_kernel<uint16_t>, a, ids);
-    if (dtype == WDD_FRAME_F32) return cudaLaunchKernelEx(&cfg, project_tc_kernel<float>, a, ids);
+    if (dtype == WDD_FRAME_U16)
+        return cudaLaunchKernelEx(&cfg, project_tc_kernel<uint16_t>, a, segs, ids);
+    if (dtype == WDD_FRAME_F32) return cudaLaunchKernelEx(&cfg, project_tc_kernel<float>, a, segs, ids);
     return cudaErrorInvalidValue;
 }
 

@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_int64),
         ("overlap_pushes", ctypes.c_int32),
         ("accum_segment", ctypes.c_int32),
-        ("accum_mode", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("accum_mode", ctypes.c_int32), ("coalesce_frames", ctypes.c_int32),
     ]
 
 
@@ -75,6 +75,7 @@ class PlanInfo(ctypes.Structure):
         ("positions_covered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("staged", ctypes.c_int32), ("finished", ctypes.c_int32),
         ("proj_tensor", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
+        ("pending", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -147,7 +148,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 precision="fp32", frame_dtype="f32", max_batch=256, accum_depth=0,
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
                 hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False,
-                accum_segment=0, accum_mode="direct") -> Params:
+                accum_segment=0, accum_mode="direct", coalesce_frames=0) -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -165,6 +166,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.overlap_pushes = 1 if overlap_pushes else 0
     p.accum_segment = accum_segment
     p.accum_mode = ACCUM_MODE[accum_mode] if isinstance(accum_mode, str) else int(accum_mode)
+    p.coalesce_frames = coalesce_frames
     return p
 
 

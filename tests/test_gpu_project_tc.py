@@ -2,7 +2,7 @@
 
 The tensor-core projection splits the frame and the basis into FP16 hi and lo parts (uint16
 counts exactly), so its coefficients carry FP32-level error: each is held to 2e-6 relative L2
-over a batch, the level of the SIMT FP32 projection.  Shapes cover full and partial 64-column
+over a batch, the level of the SIMT FP32 projection.  Shapes cover full and partial 32-column
 chunks and detector heights above and below one 128-row tile.
 """
 import dataclasses
@@ -107,3 +107,48 @@ def test_out_of_range_float_frame_is_reported(torch_cuda):
         g.reset()
         g.push(to_source(F, "device"), idx)
         g.check_device()
+
+
+def _run(acq, F, idx, pushes, source_of=None, depth=1024, **kw):
+    # the device copy stays alive for the whole run: gathered pushes are read when launched
+    d = to_source(F, "device")
+    with gpu_plan(acq, "hg_tensor", 64, precision="split", max_batch=256, accum_depth=depth,
+                  **kw) as g:
+        pos = 0
+        pending_seen = 0
+        for i, n in enumerate(pushes):
+            src = source_of(i) if source_of else "device"
+            g.push(d[pos:pos + n] if src == "device" else F[pos:pos + n], idx[pos:pos + n])
+            pending_seen = max(pending_seen, g.info()["pending"])
+            pos += n
+        _, ph, _, _ = g.finalize()
+        g.check_device()
+        return g.copy_array("accum"), ph.cpu().numpy(), pending_seen
+
+
+def test_coalesced_pushes_match_immediate(torch_cuda):
+    """Pushes gathered into shared launches (many small ones, more than 16 per launch, some
+    crossing the 256-frame launch size) give bit-identical results to projecting every push
+    when it is made, as long as the accumulation sees the same groups of frames (one flush at
+    the end); with a 300-frame staging depth the flush points move and only rounding changes."""
+    acq = _acq(128, "u16", 1e4, seed=15, scan=(24, 25))
+    F = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    rng = np.random.default_rng(3)
+    pushes = []
+    left = len(idx)
+    while left:
+        n = int(min(left, rng.choice([1, 3, 7, 16, 64, 200, 256])))
+        pushes.append(n)
+        left -= n
+    H0, ph0, p0 = _run(acq, F, idx, pushes)
+    H1, ph1, p1 = _run(acq, F, idx, pushes, coalesce_frames=256)
+    assert p0 == 0 and p1 > 0
+    assert np.array_equal(H0, H1) and np.array_equal(ph0, ph1)
+    # pageable pushes bypass the gathering (and launch what is pending first)
+    H2, ph2, _ = _run(acq, F, idx, pushes, source_of=lambda i: "pageable" if i % 3 == 0 else "device",
+                      coalesce_frames=128)
+    assert np.array_equal(H0, H2) and np.array_equal(ph0, ph2)
+    H3, ph3, _ = _run(acq, F, idx, pushes, depth=300, coalesce_frames=256)
+    assert rel_l2(H3, H0) < 3e-6
+    assert W.phase_rel_l2(ph3.astype(np.float64), ph0.astype(np.float64)) < 1e-5
