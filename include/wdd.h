@@ -121,10 +121,16 @@ typedef struct {
                                  wdd_snapshot, wdd_finalize, wdd_reset or wdd_set_stream, or until
                                  wdd_plan_info reports pending == 0.  0 = every push is projected
                                  when it is made. */
+    double scan_rotation_rad; /* scan axes against the detector axes (the rotation of Tables 2
+                                 and 3): a scan frequency (q_y, q_x) along the scan axes shifts
+                                 the probe by (q_y cos - q_x sin, q_y sin + q_x cos) on the
+                                 detector, so +pi/2 matches detector images turned a quarter
+                                 turn as numpy's rot90 over the detector axes does.  0 = aligned. */
 } wdd_params;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
- * N/2, relative epsilon 1e-3, no overlap across pushes, accum_segment 0 (1024).  Geometry fields are zeroed and must be
+ * N/2, relative epsilon 1e-3, no overlap across pushes, accum_segment 0 (1024), no scan
+ * rotation.  Geometry fields are zeroed and must be
  * set by the caller. */
 wdd_status wdd_params_default(wdd_params* p);
 

@@ -19,7 +19,8 @@ Readings of the paper (each one is also listed in the design notes):
   R3 The 2-D eigenfunction is the tensor product of 1-D functions with sigma applied once.
   R4 Hermite-Gauss columns are built by the normalised three-term recurrence and rescaled to unit
      discrete L2 norm; sigma = R_bf / sqrt(2*(L-1)+1) with R_bf the bright-field radius in
-     pixels, sampled at x_j = j - c (c = detector centre, not estimated from data).
+     pixels, sampled at x_j = j - c (c = the detector centre N // 2 unless the caller passes
+     another, e.g. detector_center_of_mass of the frames, Sect. 5).
   R5 epsilon is relative: eps_eff = epsilon * max_{v,m} |chi_v[m]|^2 (an absolute mode exists).
   R6 Eq. 3's division by sqrt(o_0) is applied (principal root; skipped when o_0 == 0), then the
      conjugated inverse DFT of Algorithm 2 with numpy's 1/S normalisation.
@@ -27,6 +28,9 @@ Readings of the paper (each one is also listed in the design notes):
   R8 A frequency is active iff the two aperture discs overlap: |q_v| < 2 theta / lambda (strict).
   R9 Sign conventions: P_s = p(r - r_s); scan kernel exp(-2 pi i q_v . r_s); Y_v(q) =
      p(q) conj p(q + q_v); probe p(k) = [|k| <= theta/lambda] exp(-i pi lambda df |k|^2).
+  R15 Scan rotation (Tables 2 and 3): the scan-axis frequency (q_y, q_x) shifts the probe by
+     (q_y cos t - q_x sin t, q_y sin t + q_x cos t) on the detector; t = +90 degrees equals the
+     detector images turned by numpy's rot90 over their two axes.
 """
 from __future__ import annotations
 
@@ -41,7 +45,7 @@ __all__ = [
     "energy_pairs", "hg_energy_l", "OraclePlan", "build_plan", "project_operator",
     "coefficients", "phase_factor", "accumulate", "deconvolve", "finalize", "live_wdd",
     "live_wdd_per_frame", "offline_wdd", "phase_rel_l2", "complex_rel_l2", "active_mask",
-    "fourier_window_plan",
+    "fourier_window_plan", "scan_shift_det_px", "detector_center_of_mass",
 ]
 
 # CODATA 2018 constants (SI).
@@ -89,6 +93,7 @@ class Params:
     det_center_y: float | None = None  # default det_y // 2
     det_center_x: float | None = None
     eps_absolute: bool = False
+    scan_rotation_rad: float = 0.0     # scan axes relative to the detector axes (reading R15)
 
     @property
     def S(self) -> int:
@@ -133,6 +138,30 @@ def scan_shift_px(p: Params) -> tuple[np.ndarray, np.ndarray]:
     return qy, qx
 
 
+def scan_shift_det_px(p: Params, vy, vx):
+    """Shift of scan frequency (vy, vx) in detector pixels, along the detector axes.
+
+    The scan frequency vector (q_y, q_x) of scan_shift_px is given along the scan axes; with the
+    scan rotated by theta against the detector (the rotation of Tables 2 and 3) it points along
+    (q_y cos theta - q_x sin theta, q_y sin theta + q_x cos theta) on the detector (reading R15:
+    theta = +90 degrees is the detector image turned by numpy's rot90 over the last two axes).
+    """
+    qy, qx = scan_shift_px(p)
+    a, b = qy[vy], qx[vx]
+    c, s = math.cos(p.scan_rotation_rad), math.sin(p.scan_rotation_rad)
+    return c * a - s * b, s * a + c * b
+
+
+def detector_center_of_mass(frames: np.ndarray) -> tuple[float, float]:
+    """Centre of mass (row, column) of the summed frames in detector pixels: the data-estimated
+    centre for the basis sampling grid (Sect. 5)."""
+    f = np.asarray(frames, dtype=np.float64).reshape(-1, *np.shape(frames)[-2:]).sum(axis=0)
+    tot = f.sum()
+    rows = np.arange(f.shape[0], dtype=np.float64)
+    cols = np.arange(f.shape[1], dtype=np.float64)
+    return float(f.sum(axis=1) @ rows / tot), float(f.sum(axis=0) @ cols / tot)
+
+
 def bright_field_radius_px(p: Params) -> float:
     """Aperture radius theta / (lambda dk) in detector pixels."""
     return p.semiconv_rad / (p.wavelength_m * p.det_px_inv_m)
@@ -166,13 +195,14 @@ def probe_spectrum(ky_px: np.ndarray, kx_px: np.ndarray, p: Params) -> np.ndarra
 
 
 def probe_autocorrelation(p: Params, vy: int, vx: int) -> np.ndarray:
-    """Y_v(q) = p(q) * conj p(q + q_v) on the detector grid (Algorithm 1, Eq. 2 W_P)."""
-    qy_all, qx_all = scan_shift_px(p)
+    """Y_v(q) = p(q) * conj p(q + q_v) on the detector grid (Algorithm 1, Eq. 2 W_P), q_v along
+    the detector axes (scan_shift_det_px)."""
+    dy, dx = scan_shift_det_px(p, vy, vx)
     qy = np.arange(p.det_y, dtype=np.float64) - p.cy
     qx = np.arange(p.det_x, dtype=np.float64) - p.cx
     ky, kx = np.meshgrid(qy, qx, indexing="ij")
     a = probe_spectrum(ky, kx, p)
-    b = probe_spectrum(ky + qy_all[vy], kx + qx_all[vx], p)
+    b = probe_spectrum(ky + dy, kx + dx, p)
     return a * np.conj(b)
 
 

@@ -343,6 +343,8 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         return fail(WDD_ERR_INVALID_ARG, "unknown accumulation mode");
     if (p.coalesce_frames < 0 || p.coalesce_frames > kLaunchFrames)
         return fail(WDD_ERR_INVALID_ARG, "coalesce_frames must be in [0, 1024]");
+    if (!std::isfinite(p.scan_rotation_rad))
+        return fail(WDD_ERR_INVALID_ARG, "scan_rotation_rad must be finite");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -937,6 +939,39 @@ wdd_status wdd_reconstruct_noalloc(const void* weights, const void* accum, int32
                                                rank_k, static_cast<float2*>(obj), phase,
                                                static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "reconstruction without allocation");
+    return WDD_OK;
+}
+
+wdd_status wdd_detector_center(const void* frames, int64_t n, int32_t det_y, int32_t det_x,
+                               int32_t frame_dtype, double* center_y, double* center_x,
+                               wdd_stream_t stream) {
+    if (!frames || !center_y || !center_x)
+        return fail(WDD_ERR_INVALID_ARG, "frames and outputs must not be NULL");
+    if (n < 1 || det_y <= 0 || det_x <= 0 || det_y > 1024 || det_x > 1024)
+        return fail(WDD_ERR_INVALID_ARG, "n must be positive and detector sides in [1, 1024]");
+    if (frame_dtype < WDD_FRAME_U16 || frame_dtype > WDD_FRAME_F64)
+        return fail(WDD_ERR_INVALID_ARG, "unknown frame dtype");
+    cudaPointerAttributes attr{};
+    cudaError_t e = cudaPointerGetAttributes(&attr, frames);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    const void* src = nullptr;
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+        src = frames;
+    else if (attr.type == cudaMemoryTypeHost)
+        src = attr.devicePointer ? attr.devicePointer : frames;
+    else
+        return fail(WDD_ERR_INVALID_ARG, "frames must be in device or pinned host memory");
+    double sums[3] = {0.0, 0.0, 0.0};
+    e = launch_detector_center(src, n, det_y, det_x, frame_dtype, sums,
+                               static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "detector centre of mass");
+    if (!(sums[0] > 0.0) || !std::isfinite(sums[0]))
+        return fail(WDD_ERR_INVALID_ARG, "frames must have a positive finite total");
+    *center_y = sums[1] / sums[0];
+    *center_x = sums[2] / sums[0];
     return WDD_OK;
 }
 

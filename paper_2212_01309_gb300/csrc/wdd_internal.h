@@ -164,6 +164,10 @@ size_t frame_elem_bytes(int dtype);
 cudaError_t launch_hg_basis(double2* B, int n, int L, double sigma, double center, cudaStream_t st);
 cudaError_t launch_fourier_basis(double2* B, int n, double center, cudaStream_t st);
 cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStream_t st);
+// Sum of all frame values and the row- and column-weighted sums (frames readable by the device,
+// n >= 1); synchronises `st`.
+cudaError_t launch_detector_center(const void* frames, int64_t n, int Ny, int Nx, int dtype,
+                                   double sums[3], cudaStream_t st);
 cudaError_t launch_weights(const wdd_plan* P, cudaStream_t st);
 cudaError_t launch_tables(const wdd_plan* P, cudaStream_t st);
 

@@ -8,6 +8,8 @@
 
 #include <cuda_fp16.h>
 
+#include <cmath>
+
 #include "wdd_internal.h"
 
 namespace wdd {
@@ -86,7 +88,8 @@ __device__ __forceinline__ double2 probe_at(double k2, double R2, double coef) {
 }
 
 // chi_v = By^T Y_v Bx for one scan frequency v per block, Y_v(q) = p(q) conj p(q + q_v)
-// (Algorithm 1).  Y is built row block by row block in shared memory; Z accumulates in registers.
+// (Algorithm 1), with q_v the scan-axis shift (qy, qx) turned by the scan rotation (rc, rs):
+// (rc qy - rs qx, rs qy + rc qx) along the detector axes (exact for rc = 1, rs = 0).  Y is built row block by row block in shared memory; Z accumulates in registers.
 // Also folds max |chi_v[m]|^2 over the used indices into *maxbits (as ordered uint64 bits).
 template <int ZPT>
 __global__ void __launch_bounds__(kThreads)
@@ -94,7 +97,7 @@ chi_kernel(const double2* __restrict__ By, const double2* __restrict__ Bx,
            const double* __restrict__ qy, const double* __restrict__ qx,
            const uint8_t* __restrict__ used, double2* __restrict__ chi,
            unsigned long long* maxbits, int Sx, int Ny, int Nx, int Ly, int Lx,
-           double cy, double cx, double R, double R2, double coef) {
+           double cy, double cx, double R, double R2, double coef, double rc, double rs) {
     extern __shared__ double2 sm[];
     double2* sBx = sm;                          // Nx * Lx
     double2* sY = sBx + (size_t)Nx * Lx;        // kChiRows * Nx
@@ -102,8 +105,10 @@ chi_kernel(const double2* __restrict__ By, const double2* __restrict__ Bx,
     __shared__ double red[kThreads];
 
     const int v = blockIdx.x;
-    const double shy = qy[v / Sx];
-    const double shx = qx[v % Sx];
+    const double sa = qy[v / Sx];
+    const double sb = qx[v % Sx];
+    const double shy = __dsub_rn(__dmul_rn(rc, sa), __dmul_rn(rs, sb));
+    const double shx = __dadd_rn(__dmul_rn(rs, sa), __dmul_rn(rc, sb));
     const int M = Ly * Lx;
 
     for (int t = threadIdx.x; t < Nx * Lx; t += blockDim.x) sBx[t] = Bx[t];
@@ -253,7 +258,89 @@ __global__ void tables_kernel(float2* tw, uint2* tw16, int lcm, float2* twy, int
     }
 }
 
+// Detector centre of mass, pass 1: per-pixel sums over one contiguous group of frames
+// (blockIdx.y), in FP64 in frame order.  part is [groups][npix].
+template <typename FT>
+__global__ void com_partial_kernel(const FT* __restrict__ f, int64_t n, int npix, int64_t per,
+                                   double* __restrict__ part) {
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= npix) return;
+    const int64_t f0 = (int64_t)blockIdx.y * per;
+    const int64_t f1 = f0 + per < n ? f0 + per : n;
+    double s = 0.0;
+    for (int64_t t = f0; t < f1; ++t) s += (double)f[t * npix + pix];
+    part[(size_t)blockIdx.y * npix + pix] = s;
+}
+
+// Pass 2 (one block of kComThreads): pixel sums over the groups in group order, then the total
+// and the row- and column-weighted totals, reduced over the block in a fixed tree.
+constexpr int kComThreads = 1024;
+__global__ void __launch_bounds__(kComThreads)
+com_final_kernel(const double* __restrict__ part, int groups, int Ny, int Nx,
+                 double* __restrict__ out) {
+    __shared__ double red[3][kComThreads];
+    const int npix = Ny * Nx;
+    double s0 = 0.0, sy = 0.0, sx = 0.0;
+    for (int pix = threadIdx.x; pix < npix; pix += kComThreads) {
+        double v = 0.0;
+        for (int g = 0; g < groups; ++g) v += part[(size_t)g * npix + pix];
+        s0 += v;
+        sy += v * (double)(pix / Nx);
+        sx += v * (double)(pix % Nx);
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = sy;
+    red[2][threadIdx.x] = sx;
+    __syncthreads();
+    for (int w = kComThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
 }  // namespace
+
+cudaError_t launch_detector_center(const void* frames, int64_t n, int Ny, int Nx, int dtype,
+                                   double sums[3], cudaStream_t st) {
+    const int npix = Ny * Nx;
+    const int pix_blocks = (npix + kThreads - 1) / kThreads;
+    // about four blocks per SM over the pixel blocks and frame groups
+    int64_t groups = (4 * 152 + pix_blocks - 1) / pix_blocks;
+    if (groups > n) groups = n;
+    if (groups > 65535) groups = 65535;
+    if (groups < 1) groups = 1;
+    const int64_t per = (n + groups - 1) / groups;
+    groups = (n + per - 1) / per;
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * ((size_t)groups * npix + 3));
+    if (e != cudaSuccess) return e;
+    dim3 grid(pix_blocks, (unsigned)groups);
+    switch (dtype) {
+        case WDD_FRAME_U16:
+            com_partial_kernel<<<grid, kThreads, 0, st>>>(static_cast<const uint16_t*>(frames), n,
+                                                          npix, per, d + 3);
+            break;
+        case WDD_FRAME_F32:
+            com_partial_kernel<<<grid, kThreads, 0, st>>>(static_cast<const float*>(frames), n,
+                                                          npix, per, d + 3);
+            break;
+        default:
+            com_partial_kernel<<<grid, kThreads, 0, st>>>(static_cast<const double*>(frames), n,
+                                                          npix, per, d + 3);
+            break;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        com_final_kernel<<<1, kComThreads, 0, st>>>(d + 3, (int)groups, Ny, Nx, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, d, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(d);
+    return e != cudaSuccess ? e : e2;
+}
 
 cudaError_t launch_hg_basis(double2* B, int n, int L, double sigma, double center, cudaStream_t st) {
     hg_basis_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, n, L, sigma, center);
@@ -288,6 +375,7 @@ cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStr
     double R2 = P->R * P->R;
     double coef = 3.14159265358979323846 * P->lambda * P->p.defocus_m *
                   (P->p.det_px_inv_m * P->p.det_px_inv_m);
+    const double rc = std::cos(P->p.scan_rotation_rad), rs = std::sin(P->p.scan_rotation_rad);
 #define WDD_CHI(Z)                                                                                \
     do {                                                                                          \
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(chi_kernel<Z>));                 \
@@ -295,7 +383,7 @@ cudaError_t launch_chi(const wdd_plan* P, unsigned long long* d_maxbits, cudaStr
             chi_kernel<Z><<<P->S, kThreads, smem, st>>>(P->d_By, P->d_Bx, P->d_qy, P->d_qx,       \
                                                         d_used, P->d_chi, d_maxbits, P->Sx,       \
                                                         P->Ny, P->Nx, P->Ly, P->Lx, P->cy, P->cx, \
-                                                        P->R, R2, coef);                          \
+                                                        P->R, R2, coef, rc, rs);                  \
     } while (0)
     if (zpt <= 1) WDD_CHI(1);
     else if (zpt <= 2) WDD_CHI(2);

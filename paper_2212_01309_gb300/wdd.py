@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("overlap_pushes", ctypes.c_int32),
         ("accum_segment", ctypes.c_int32),
         ("accum_mode", ctypes.c_int32), ("coalesce_frames", ctypes.c_int32),
+        ("scan_rotation_rad", ctypes.c_double),
     ]
 
 
@@ -103,6 +104,10 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_reconstruct_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "wdd_detector_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "wdd_get_hit_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wdd_copy_array": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -148,7 +153,8 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 precision="fp32", frame_dtype="f32", max_batch=256, accum_depth=0,
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
                 hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False,
-                accum_segment=0, accum_mode="direct", coalesce_frames=0) -> Params:
+                accum_segment=0, accum_mode="direct", coalesce_frames=0,
+                scan_rotation_rad=0.0) -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -167,6 +173,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.accum_segment = accum_segment
     p.accum_mode = ACCUM_MODE[accum_mode] if isinstance(accum_mode, str) else int(accum_mode)
     p.coalesce_frames = coalesce_frames
+    p.scan_rotation_rad = scan_rotation_rad
     return p
 
 
@@ -341,6 +348,26 @@ class Plan:
 def selftest_bounded_wait(wait_ns: int = 50_000_000) -> int:
     """Runs the device bounded-wait self test; returns the status code (ERR_TIMEOUT expected)."""
     return int(lib().wdd_selftest_bounded_wait(int(wait_ns)))
+
+
+def detector_center(frames, stream=None) -> tuple[float, float]:
+    """Centre of mass (row, column) of frames [n, det_y, det_x] (wdd_detector_center): a torch
+    tensor on the GPU or in pinned host memory, of dtype uint16, float32 or float64."""
+    import torch
+    dt = {torch.uint16: "u16", torch.float32: "f32", torch.float64: "f64"}.get(frames.dtype)
+    if dt is None:
+        raise TypeError(f"unsupported frame dtype {frames.dtype}")
+    if frames.dim() != 3 or not frames.is_contiguous():
+        raise ValueError("frames must be a contiguous [n, det_y, det_x] tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    cy, cx = ctypes.c_double(), ctypes.c_double()
+    n, ny, nx = frames.shape
+    _check(lib().wdd_detector_center(ctypes.c_void_p(_ptr(frames)), n, ny, nx, FRAME_DTYPE[dt],
+                                     ctypes.byref(cy), ctypes.byref(cx),
+                                     ctypes.c_void_p(int(stream.cuda_stream))),
+           "wdd_detector_center")
+    return cy.value, cx.value
 
 
 def reconstruct_noalloc(weights, accum, scan_y: int, scan_x: int, rank_k: int, obj, phase=None,

@@ -53,12 +53,12 @@ def test_struct_layout_matches_c(wdd, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "wdd.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(wdd_params),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(wdd_params),"
         " offsetof(wdd_params, rank_k), offsetof(wdd_params, det_center_y),"
         " offsetof(wdd_params, hbm_budget_bytes), sizeof(wdd_result), sizeof(wdd_plan_info),"
         " offsetof(wdd_params, overlap_pushes), offsetof(wdd_params, proj_cluster),"
         " offsetof(wdd_params, accum_segment), offsetof(wdd_params, accum_mode),"
-        " offsetof(wdd_plan_info, proj_tensor));"
+        " offsetof(wdd_plan_info, proj_tensor), offsetof(wdd_params, scan_rotation_rad));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -69,7 +69,8 @@ def test_struct_layout_matches_c(wdd, tmp_path):
     assert got == [ctypes.sizeof(P), P.rank_k.offset, P.det_center_y.offset,
                    P.hbm_budget_bytes.offset, ctypes.sizeof(wdd.Result),
                    ctypes.sizeof(wdd.PlanInfo), P.overlap_pushes.offset, P.proj_cluster.offset,
-                   P.accum_segment.offset, P.accum_mode.offset, wdd.PlanInfo.proj_tensor.offset]
+                   P.accum_segment.offset, P.accum_mode.offset, wdd.PlanInfo.proj_tensor.offset,
+                   P.scan_rotation_rad.offset]
 
 
 def test_invalid_params_rejected_on_host(wdd):
