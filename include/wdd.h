@@ -306,6 +306,64 @@ typedef enum {
 wdd_status wdd_copy_array(wdd_plan* plan, int32_t which, void* host_dst, int64_t bytes,
                           int64_t* written);
 
+/* Centre of mass of n detector frames (row, column, in pixels): sum over frames and pixels of
+ * I[i][j] (i, j) / sum of I, accumulated in FP64 in a fixed order (bit-reproducible).  This is
+ * the data-estimated centre of the basis sampling grid (Sect. 5 samples the Hermite-Gauss
+ * functions around the centre of mass); pass it as det_center_y / det_center_x to
+ * wdd_plan_create.  frames: n x det_y x det_x values of frame_dtype, row-major, in device or
+ * pinned host memory (read in place), borrowed for the call.  Runs on `stream` and returns when
+ * the result is on the host; allocates a small scratch buffer.  Errors: INVALID_ARG (NULL
+ * pointers, n < 1, sizes out of range, pageable frames, a total that is not positive), CUDA. */
+wdd_status wdd_detector_center(const void* frames, int64_t n, int32_t det_y, int32_t det_x,
+                               int32_t frame_dtype, double* center_y, double* center_x,
+                               wdd_stream_t stream);
+
+/* ---- Classical (offline) WDD on the whole 4-D dataset (Eq. 2 and 3) --------------------------
+ * The method live WDD reformulates, run on the GPU for comparison and validation:
+ *   G(v, q)  = forward FFT over both scan axes of I_s(q)                         (Eq. 2)
+ *   W_O(v,r) = IFFT_q(ifftshift_q G(v, .)) conj(W_P) / (|W_P|^2 + eps_eff),
+ *              W_P = IFFT_q(ifftshift_q Y_v), Y_v(q) = p(q) conj p(q + q_v)       (Eq. 2)
+ *   o_v      = sum_r W_O(v, r) (F_r(W_O) at q = 0), 0 for inactive v             (Eq. 3)
+ * then the normalisation by sqrt(o_0) and conjugated inverse DFT of wdd_snapshot.  Inverse
+ * transforms carry numpy's 1/(N_y N_x) factor; eps_eff = epsilon * max_{v,r} |W_P|^2 unless
+ * eps_absolute.  FP32 transforms (twiddles built in FP64), Y_v in FP64.
+ * Parameters used: scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, voltage_v,
+ * semiconv_rad, defocus_m, epsilon, eps_absolute, frame_dtype, scan_rotation_rad,
+ * hbm_budget_bytes; the detector centre must be the default det / 2 (the zero frequency moves to
+ * pixel 0 by an integer roll).  Other fields are ignored.  Device memory: two complex64
+ * [S][det_y][det_x] arrays (the scan spectrum and the Wiener kernel) plus O(S). */
+typedef struct wdd_offline_plan wdd_offline_plan;
+
+/* Builds the Wiener kernel for every scan frequency (synchronous).  Errors: INVALID_ARG,
+ * UNSUPPORTED (detector centre not det / 2, sizes), OUT_OF_MEMORY (budget or allocation), CUDA. */
+wdd_status wdd_offline_plan_create(const wdd_params* p, wdd_offline_plan** out);
+/* Device bytes such a plan would hold, without touching the GPU. */
+wdd_status wdd_offline_footprint(const wdd_params* p, int64_t* bytes);
+/* Reconstructs from all S = scan_y * scan_x frames: frames [S][det_y][det_x] of frame_dtype in
+ * raster scan order (s = s_y * scan_x + s_x), in device or pinned host memory, borrowed until
+ * `stream` has passed the call.  Writes out->obj (complex64 [scan_y][scan_x]) and out->phase
+ * (f32, may be NULL) in stream order; frames_seen = positions_covered = S.  Calls on one plan
+ * must be ordered (one stream, or synchronised).  Errors: INVALID_ARG (NULL pointers, pageable
+ * frames), CUDA. */
+wdd_status wdd_offline_reconstruct(wdd_offline_plan* plan, const void* frames, wdd_result* out,
+                                   wdd_stream_t stream);
+typedef enum {
+    WDD_OFFLINE_SPECTRUM = 0, /* complex64 [S] o_v of the last reconstruction (before the
+                                 normalisation by sqrt(o_0))                                */
+    WDD_OFFLINE_WIENER = 1,   /* complex64 [S][det_y][det_x] conj(W_P) / (|W_P|^2 + eps_eff),
+                                 r in numpy ifft2 order, zero for inactive v               */
+    WDD_OFFLINE_MASK = 2      /* uint8 [S] 1 = active frequency                             */
+} wdd_offline_array;
+/* Synchronously copies an array into host memory (bytes >= its size; *written = bytes copied). */
+wdd_status wdd_offline_copy_array(wdd_offline_plan* plan, int32_t which, void* host_dst,
+                                  int64_t bytes, int64_t* written);
+/* Device bytes held, active frequencies, 1 if one CTA transforms a whole detector plane, and
+ * eps_eff.  Any output pointer may be NULL. */
+wdd_status wdd_offline_get_info(const wdd_offline_plan* plan, int64_t* device_bytes,
+                                int32_t* n_active, int32_t* fused, double* eps_eff);
+/* Frees the plan (synchronises the device first). */
+wdd_status wdd_offline_plan_destroy(wdd_offline_plan* plan);
+
 /* Status name ("WDD_OK", ...) and the calling thread's last error detail. */
 const char* wdd_status_string(wdd_status s);
 const char* wdd_last_error(void);

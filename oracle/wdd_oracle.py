@@ -44,8 +44,9 @@ __all__ = [
     "bright_field_radius_px", "probe_spectrum", "probe_autocorrelation", "hg_functions_1d",
     "energy_pairs", "hg_energy_l", "OraclePlan", "build_plan", "project_operator",
     "coefficients", "phase_factor", "accumulate", "deconvolve", "finalize", "live_wdd",
-    "live_wdd_per_frame", "offline_wdd", "phase_rel_l2", "complex_rel_l2", "active_mask",
-    "fourier_window_plan", "scan_shift_det_px", "detector_center_of_mass",
+    "live_wdd_per_frame", "offline_wdd", "offline_probe_wigner", "offline_wdd_frequency",
+    "phase_rel_l2", "complex_rel_l2", "active_mask", "fourier_window_plan", "scan_shift_det_px",
+    "detector_center_of_mass",
 ]
 
 # CODATA 2018 constants (SI).
@@ -467,6 +468,32 @@ def live_wdd_per_frame(frames: np.ndarray, scan_idx: np.ndarray, plan: OraclePla
 # Classical (offline) WDD, Eq. 2 and Eq. 3
 # ---------------------------------------------------------------------------------------------
 
+def offline_probe_wigner(p: Params, vy: int, vx: int) -> np.ndarray:
+    """W_P(v, r) = F_q^-1(Y_v): the inverse detector DFT of the probe autocorrelation after moving
+    q = 0 to index 0 (Eq. 2; numpy ifft2 normalisation)."""
+    return np.fft.ifft2(np.fft.ifftshift(probe_autocorrelation(p, vy, vx)))
+
+
+def offline_wdd_frequency(frames: np.ndarray, scan_idx: np.ndarray, p: Params, vy: int, vx: int,
+                          eps_eff: float) -> complex:
+    """o_v of classical WDD for one scan frequency, with the scan transform written as the plain
+    sum G_v(q) = sum_s exp(-2 pi i q_v . r_s) I_s(q) over the given frames (Eq. 2), then
+    W_O = F_q^-1(G_v) conj(W_P) / (|W_P|^2 + eps_eff) and o_v = sum_r W_O (Eq. 3).  Lets a large
+    dataset be checked one frequency at a time; eps_eff is passed in (it is a maximum over all
+    frequencies).  Inactive frequencies give 0."""
+    if p.cy != p.det_y // 2 or p.cx != p.det_x // 2:
+        raise ValueError("offline WDD assumes the detector centre at N//2")
+    v = vy * p.scan_x + vx
+    if not active_mask(p)[v]:
+        return 0j
+    E = phase_factor(p, np.array([v]), np.asarray(scan_idx))[0]
+    I = np.asarray(frames, dtype=np.float64).reshape(len(E), -1)
+    Gv = (E @ I).reshape(p.det_y, p.det_x)
+    GP = np.fft.ifft2(np.fft.ifftshift(Gv))
+    WP = offline_probe_wigner(p, vy, vx)
+    return complex(np.sum(GP * np.conj(WP) / (np.abs(WP) ** 2 + eps_eff)))
+
+
 def offline_wdd(frames: np.ndarray, p: Params) -> np.ndarray:
     """Classical WDD on the whole 4-D dataset; returns the spectrum o (S complex).
 
@@ -482,7 +509,7 @@ def offline_wdd(frames: np.ndarray, p: Params) -> np.ndarray:
     WP = np.empty((p.scan_y, p.scan_x, p.det_y, p.det_x), dtype=np.complex128)
     for vy in range(p.scan_y):
         for vx in range(p.scan_x):
-            WP[vy, vx] = np.fft.ifft2(np.fft.ifftshift(probe_autocorrelation(p, vy, vx)))
+            WP[vy, vx] = offline_probe_wigner(p, vy, vx)
     eps_eff = p.epsilon if p.eps_absolute else p.epsilon * float(np.max(np.abs(WP) ** 2))
     GP = np.fft.ifft2(np.fft.ifftshift(G, axes=(2, 3)), axes=(2, 3))
     WO = GP * np.conj(WP) / (np.abs(WP) ** 2 + eps_eff)

@@ -40,15 +40,39 @@ constexpr double kElectronMass = 9.1093837015e-31;
 constexpr double kCharge = 1.602176634e-19;
 constexpr double kLight = 299792458.0;
 
+int signed_freq(int v, int n) { return (v <= (n - 1) / 2) ? v : v - n; }
+
+}  // namespace
+
 double electron_wavelength(double volts) {
     double ev = kCharge * volts;
     double rel = 1.0 + ev / (2.0 * kElectronMass * kLight * kLight);
     return kPlanck / std::sqrt(2.0 * kElectronMass * ev * rel);
 }
 
-int signed_freq(int v, int n) { return (v <= (n - 1) / 2) ? v : v - n; }
-
-}  // namespace
+int scan_geometry(const wdd_params& p, double R, std::vector<double>& qy, std::vector<double>& qx,
+                  std::vector<uint8_t>& mask) {
+    const int Sy = p.scan_y, Sx = p.scan_x;
+    qy.assign(Sy, 0.0);
+    qx.assign(Sx, 0.0);
+    double den_y = ((double)Sy * p.scan_step_m) * p.det_px_inv_m;
+    double den_x = ((double)Sx * p.scan_step_m) * p.det_px_inv_m;
+    for (int v = 0; v < Sy; ++v) qy[v] = (double)signed_freq(v, Sy) / den_y;
+    for (int v = 0; v < Sx; ++v) qx[v] = (double)signed_freq(v, Sx) / den_x;
+    mask.assign((size_t)Sy * Sx, 0);
+    int n_active = 0;
+    double lim = 4.0 * (R * R);
+    for (int vy = 0; vy < Sy; ++vy)
+        for (int vx = 0; vx < Sx; ++vx) {
+            double a = qy[vy] * qy[vy];
+            double b = qx[vx] * qx[vx];
+            double d2 = a + b;
+            uint8_t on = d2 < lim ? 1 : 0;
+            mask[(size_t)vy * Sx + vx] = on;
+            n_active += on;
+        }
+    return n_active;
+}
 
 cudaError_t allow_max_dynamic_smem(const void* func) {
     int dev = 0, optin = 0;
@@ -452,26 +476,9 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
     }
 
     // ---- shifts and active mask (Sect. 6.2, Eq. 15; R8: |q_v| < 2 R strictly) ----------------------
-    std::vector<double> qy(P->Sy), qx(P->Sx);
-    {
-        double den_y = ((double)P->Sy * p.scan_step_m) * p.det_px_inv_m;
-        double den_x = ((double)P->Sx * p.scan_step_m) * p.det_px_inv_m;
-        for (int v = 0; v < P->Sy; ++v) qy[v] = (double)signed_freq(v, P->Sy) / den_y;
-        for (int v = 0; v < P->Sx; ++v) qx[v] = (double)signed_freq(v, P->Sx) / den_x;
-    }
-    std::vector<uint8_t> mask(P->S);
-    {
-        double lim = 4.0 * (P->R * P->R);
-        for (int vy = 0; vy < P->Sy; ++vy)
-            for (int vx = 0; vx < P->Sx; ++vx) {
-                double a = qy[vy] * qy[vy];
-                double b = qx[vx] * qx[vx];
-                double d2 = a + b;
-                uint8_t on = d2 < lim ? 1 : 0;
-                mask[vy * P->Sx + vx] = on;
-                P->n_active += on;
-            }
-    }
+    std::vector<double> qy, qx;
+    std::vector<uint8_t> mask;
+    P->n_active = scan_geometry(p, P->R, qy, qx, mask);
 
     // ---- memory budget -----------------------------------------------------------------
     int64_t need = planned_bytes(P);

@@ -1,5 +1,5 @@
 // Device helpers shared by the kernels of libwdd.so: shared-memory addresses, mbarriers with
-// bounded waits, and 1-D TMA bulk copies.
+// bounded waits, 1-D TMA bulk copies, and the analytic probe spectrum.
 #pragma once
 
 #include <stdint.h>
@@ -68,6 +68,16 @@ static __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, u
             "r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Probe spectrum at a detector point k (pixels) given its squared radius k2 (already rounded):
+// A(k) exp(-i coef k2) with A the hard-edged aperture |k|^2 <= R^2 (Algorithm 1 initialisation).
+static __device__ __forceinline__ double2 probe_at(double k2, double R2, double coef) {
+    if (!(k2 <= R2)) return make_double2(0.0, 0.0);
+    if (coef == 0.0) return make_double2(1.0, 0.0);
+    double s, c;
+    sincos(__dmul_rn(coef, k2), &s, &c);
+    return make_double2(c, -s);
 }
 
 }  // namespace wdd

@@ -208,6 +208,18 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
                                     cudaStream_t st);
 cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st);
 cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st);
+// The normalisation and conjugated inverse DFT of Eq. 3 on any spectrum o [Sy][Sx] (tmp: [S]
+// scratch; twy/twx: exp(+2 pi i m / n) tables written by launch_idft_tables).
+cudaError_t launch_idft_tables(float2* twy, int Sy, float2* twx, int Sx, cudaStream_t st);
+cudaError_t launch_idft(const float2* o, const float2* twx, const float2* twy, float2* tmp, int Sy,
+                        int Sx, float2* obj, float* phase, cudaStream_t st);
+
+// ---- host geometry shared by the live and the classical plans (Sect. 6.2) -------------------
+double electron_wavelength(double volts);
+// Probe shift per scan frequency (detector pixels along the scan axes) and the overlap mask
+// |q_v| < 2 R (Eq. 15, strict); returns the number of active frequencies.
+int scan_geometry(const wdd_params& p, double R, std::vector<double>& qy, std::vector<double>& qx,
+                  std::vector<uint8_t>& mask);
 
 // Reconstruction that allocates nothing (see wdd_reconstruct_noalloc): the device address of the
 // file-scope scratch array for `device` (resolved on first use), its size, and the launcher.

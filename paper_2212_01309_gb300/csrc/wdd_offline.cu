@@ -1,0 +1,858 @@
+// Classical (offline) WDD on the GPU: Eq. 2 and Eq. 3 over the whole 4-D dataset.
+//
+//   G(v, q)  = sum_s exp(-2 pi i q_v . r_s) I_s(q)         forward FFT over both scan axes
+//   G'(v, r) = IFFT_q( ifftshift_q G(v, .) )                 inverse FFT over the detector
+//   W_O      = G' conj(W_P) / (|W_P|^2 + eps_eff),  W_P = IFFT_q( ifftshift_q Y_v )
+//   o_v      = sum_r W_O(v, r)                                (F_r(W_O) at q = 0)
+//
+// followed by the normalisation by sqrt(o_0) and the conjugated inverse DFT shared with the live
+// path.  Every transform is a batch of 1-D transforms staged through shared memory: radix-2
+// decimation in time for power-of-two lengths (inputs placed in bit-reversed order as they are
+// loaded) and a direct DFT with exact integer twiddle indices for other lengths, in FP32 with
+// twiddles built in FP64.  Each pass reads and writes HBM once; the detector pass keeps one scan
+// frequency's whole detector plane in shared memory when it fits and multiplies by the Wiener
+// kernel on the way out, so G' never reaches HBM.  Larger detectors take a row pass and a column
+// pass, the second one fused with the product and a per-block partial sum.
+//
+// The Wiener kernel conj(W_P) / (|W_P|^2 + eps_eff) is built once per plan: Y_v in FP64 exactly
+// as the live plan evaluates it (the analytic probe at the shifted point), the same detector
+// transform in FP32, eps_eff = epsilon * max |W_P|^2 (relative, reading R5) and the division.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wdd_device.cuh"
+#include "wdd_internal.h"
+
+struct wdd_offline_plan {
+    wdd_params p{};
+    int Sy = 0, Sx = 0, S = 0, Ny = 0, Nx = 0, npix = 0;
+    double lambda = 0, R = 0, eps_eff = 0;
+    int n_active = 0;
+    int fused = 0;               // 1: one CTA holds a whole detector plane
+    int rb = 0, cp = 0, ncb = 0; // two-pass detector transform: rows per CTA, columns per CTA, blocks
+    float2* d_G = nullptr;       // [S][Ny][Nx] scan spectrum (work array)
+    float2* d_K = nullptr;       // [S][Ny][Nx] Wiener kernel conj(W_P) / (|W_P|^2 + eps_eff)
+    uint8_t* d_mask = nullptr;   // [S]
+    double* d_qy = nullptr;      // [Sy] probe shift per frequency row, detector pixels
+    double* d_qx = nullptr;      // [Sx]
+    float2* d_tw_sy = nullptr;   // [Sy] exp(-2 pi i j / Sy)
+    float2* d_tw_sx = nullptr;   // [Sx]
+    float2* d_tw_dy = nullptr;   // [Ny] exp(-2 pi i j / Ny) (conjugated for the inverse)
+    float2* d_tw_dx = nullptr;   // [Nx]
+    float2* d_twy_inv = nullptr; // [Sy] exp(+2 pi i j / Sy) (final inverse DFT)
+    float2* d_twx_inv = nullptr; // [Sx]
+    float2* d_o = nullptr;       // [S] spectrum o_v
+    float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
+    float2* d_part = nullptr;    // [S][ncb] partial sums of the two-pass detector transform
+    unsigned* d_max = nullptr;   // [1] max |W_P|^2 (float bits)
+    std::vector<wdd::DevBuf> allocs;
+    int64_t device_bytes = 0;
+};
+
+namespace wdd {
+namespace {
+
+constexpr int kOffThreads = 256;
+constexpr int kDetThreads = 512;
+constexpr int kScanLineElems = 8192;    // elements staged per scan-axis CTA (64 KB)
+constexpr int kFusedPow2Pix = 16384;    // detector planes up to 128 KB take the fused pass
+constexpr int kFusedDftPix = 12288;     // two buffers for the direct DFT
+
+wdd_status off_fail(wdd_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+wdd_status off_cuda_fail(cudaError_t e, const char* where) {
+    return off_fail(WDD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int log2_exact(int n) {  // log2(n) for powers of two, else -1
+    if (n <= 0 || (n & (n - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+__device__ __forceinline__ int brev_bits(int j, int logn) {
+    return logn > 0 ? (int)(__brev((unsigned)j) >> (32 - logn)) : 0;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 as_c(uint16_t v) { return make_float2((float)v, 0.f); }
+__device__ __forceinline__ float2 as_c(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 as_c(double v) { return make_float2((float)v, 0.f); }
+__device__ __forceinline__ float2 as_c(float2 v) { return v; }
+
+// In-place radix-2 decimation-in-time transforms of `lines` lines of length 2^logn held in
+// shared memory in bit-reversed order: element i of line l at buf[l * ls + i * es].
+// tw[j] = exp(-2 pi i j / n) for j < n / 2; INV uses the conjugate (no 1/n factor).
+// line_fastest: consecutive threads take consecutive lines (bank-conflict free when es > 1).
+template <bool INV>
+__device__ void fft_lines_pow2(float2* buf, int logn, int lines, int es, int ls, const float2* tw,
+                               bool line_fastest) {
+    if (logn <= 0) return;
+    const int half = 1 << (logn - 1);
+    const int total = lines * half;
+    for (int s = 0; s < logn; ++s) {
+        const int h = 1 << s;
+        for (int b = threadIdx.x; b < total; b += blockDim.x) {
+            int l, t;
+            if (line_fastest) {
+                l = b % lines;
+                t = b / lines;
+            } else {
+                l = b >> (logn - 1);
+                t = b & (half - 1);
+            }
+            const int k = t & (h - 1);
+            const int i0 = ((t >> s) << (s + 1)) + k;
+            float2 w = tw[k << (logn - 1 - s)];
+            if (INV) w.y = -w.y;
+            float2* p0 = buf + (size_t)l * ls + (size_t)i0 * es;
+            float2* p1 = p0 + (size_t)h * es;
+            const float2 a = *p0;
+            const float2 c = cmulf(w, *p1);
+            *p0 = make_float2(a.x + c.x, a.y + c.y);
+            *p1 = make_float2(a.x - c.x, a.y - c.y);
+        }
+        __syncthreads();
+    }
+}
+
+// One output of a direct DFT of length n: sum_m in[m * es] w^(j m), w = exp(-/+ 2 pi i / n),
+// with the exact twiddle index (j m) mod n into tw[j] = exp(-2 pi i j / n), j < n.
+template <bool INV>
+__device__ __forceinline__ float2 dft_point(const float2* in, int es, int n, int j,
+                                            const float2* tw) {
+    float re = 0.f, im = 0.f;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const float2 a = in[(size_t)i * es];
+        float2 w = tw[m];
+        if (INV) w.y = -w.y;
+        re = fmaf(a.x, w.x, fmaf(-a.y, w.y, re));
+        im = fmaf(a.x, w.y, fmaf(a.y, w.x, im));
+        m += j;
+        if (m >= n) m -= n;
+    }
+    return make_float2(re, im);
+}
+
+// Fixed-order block reductions (valid in thread 0).
+__device__ float2 block_sum2(float2 v, float2* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float2 s = make_float2(0.f, 0.f);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = make_float2(s.x + red[w].x, s.y + red[w].y);
+    return s;
+}
+
+__device__ float block_max(float v, float* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float m = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    return m;
+}
+
+// exp(-2 pi i j / n), j < n, FP64-built.
+__global__ void twiddle_kernel(float2* tw, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)j / (double)n, &s, &c);
+    tw[j] = make_float2((float)c, (float)-s);
+}
+
+// Forward transform along one scan axis for a block of P detector pixels.  Line `o`
+// (blockIdx.y) starts at o * outer_stride; element j of the axis sits j * es further; the P
+// pixels are contiguous (coalesced).  src may be the frames (first axis) or dst itself.
+template <typename T, bool PW2>
+__global__ void __launch_bounds__(kOffThreads)
+scan_axis_kernel(const T* src, float2* dst, const float2* __restrict__ tw_g, int n, int logn,
+                 int P, int npix, int64_t outer_stride, int64_t es) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm;        // n
+    float2* buf = sm + n;   // n * P
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = tw_g[t];
+    const int q0 = blockIdx.x * P;
+    const int np = min(P, npix - q0);
+    const int64_t base = (int64_t)blockIdx.y * outer_stride + q0;
+    for (int t = threadIdx.x; t < n * P; t += blockDim.x) {
+        const int j = t / P, p = t - (t / P) * P;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < np) v = as_c(src[base + (int64_t)j * es + p]);
+        const int pos = PW2 ? brev_bits(j, logn) : j;
+        buf[pos * P + p] = v;
+    }
+    __syncthreads();
+    if (PW2) {
+        fft_lines_pow2<false>(buf, logn, P, P, 1, tw, true);
+        for (int t = threadIdx.x; t < n * P; t += blockDim.x) {
+            const int j = t / P, p = t - (t / P) * P;
+            if (p < np) dst[base + (int64_t)j * es + p] = buf[t];
+        }
+    } else {
+        for (int t = threadIdx.x; t < n * P; t += blockDim.x) {
+            const int j = t / P, p = t - (t / P) * P;
+            if (p < np) dst[base + (int64_t)j * es + p] = dft_point<false>(buf + p, P, n, j, tw);
+        }
+    }
+}
+
+// Whole detector plane of one scan frequency (blockIdx.x) in shared memory: ifftshift on load,
+// inverse 2-D transform, then
+//   MODE 0: o_v = scale * sum_r G'(r) K(r)   (inactive v: 0)
+//   MODE 1: plane = scale * G' written back in place, max |.|^2 folded into *maxbits.
+template <int MODE, bool PW2>
+__global__ void __launch_bounds__(kDetThreads)
+det_fused_kernel(float2* G, const float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                 float2* __restrict__ o, unsigned* __restrict__ maxbits,
+                 const float2* __restrict__ twy_g, const float2* __restrict__ twx_g, int Ny,
+                 int Nx, int logy, int logx, float scale) {
+    extern __shared__ float2 sm[];
+    __shared__ float2 red2[kDetThreads / 32];
+    __shared__ float redf[kDetThreads / 32];
+    const int npix = Ny * Nx;
+    const int nty = PW2 ? Ny / 2 : Ny, ntx = PW2 ? Nx / 2 : Nx;
+    float2* twy = sm;
+    float2* twx = twy + nty;
+    float2* A = twx + ntx;
+    float2* B = A + npix;   // direct-DFT path only
+    const int v = blockIdx.x;
+    if (MODE == 0 && !mask[v]) {
+        if (threadIdx.x == 0) o[v] = make_float2(0.f, 0.f);
+        return;
+    }
+    for (int t = threadIdx.x; t < nty; t += blockDim.x) twy[t] = twy_g[t];
+    for (int t = threadIdx.x; t < ntx; t += blockDim.x) twx[t] = twx_g[t];
+    float2* g = G + (size_t)v * npix;
+    const int hy = Ny / 2, hx = Nx / 2;
+    for (int e = threadIdx.x; e < npix; e += blockDim.x) {
+        const int qy = e / Nx, qx = e - (e / Nx) * Nx;
+        int jy = qy - hy, jx = qx - hx;
+        if (jy < 0) jy += Ny;
+        if (jx < 0) jx += Nx;
+        if (PW2) {
+            jy = brev_bits(jy, logy);
+            jx = brev_bits(jx, logx);
+        }
+        A[jy * Nx + jx] = g[e];
+    }
+    __syncthreads();
+    float2 acc = make_float2(0.f, 0.f);
+    float mx = 0.f;
+    const float2* kv = K + (size_t)v * npix;
+    if (PW2) {
+        fft_lines_pow2<true>(A, logx, Ny, 1, Nx, twx, false);   // rows
+        fft_lines_pow2<true>(A, logy, Nx, Nx, 1, twy, true);    // columns
+        for (int e = threadIdx.x; e < npix; e += blockDim.x) {
+            const float2 val = A[e];
+            if (MODE == 0) {
+                const float2 k = kv[e];
+                acc.x = fmaf(val.x, k.x, fmaf(-val.y, k.y, acc.x));
+                acc.y = fmaf(val.x, k.y, fmaf(val.y, k.x, acc.y));
+            } else {
+                const float2 w = make_float2(val.x * scale, val.y * scale);
+                g[e] = w;
+                mx = fmaxf(mx, w.x * w.x + w.y * w.y);
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < npix; e += blockDim.x) {
+            const int jy = e / Nx, rx = e - (e / Nx) * Nx;
+            B[e] = dft_point<true>(A + (size_t)jy * Nx, 1, Nx, rx, twx);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < npix; e += blockDim.x) {
+            const int ry = e / Nx, rx = e - (e / Nx) * Nx;
+            const float2 val = dft_point<true>(B + rx, Nx, Ny, ry, twy);
+            if (MODE == 0) {
+                const float2 k = kv[e];
+                acc.x = fmaf(val.x, k.x, fmaf(-val.y, k.y, acc.x));
+                acc.y = fmaf(val.x, k.y, fmaf(val.y, k.x, acc.y));
+            } else {
+                const float2 w = make_float2(val.x * scale, val.y * scale);
+                g[e] = w;
+                mx = fmaxf(mx, w.x * w.x + w.y * w.y);
+            }
+        }
+    }
+    if (MODE == 0) {
+        const float2 s = block_sum2(acc, red2);
+        if (threadIdx.x == 0) o[v] = make_float2(s.x * scale, s.y * scale);
+    } else {
+        const float m = block_max(mx, redf);
+        if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
+    }
+}
+
+// Two-pass detector transform, pass 1: ifftshift along x and the inverse transform of RB rows
+// (blockIdx.y) of one scan frequency (blockIdx.x), in place.  The y shift waits for pass 2.
+template <bool PW2>
+__global__ void __launch_bounds__(kOffThreads)
+det_rows_kernel(float2* G, const float2* __restrict__ twx_g, int Ny, int Nx, int logx, int RB) {
+    extern __shared__ float2 sm[];
+    const int ntx = PW2 ? Nx / 2 : Nx;
+    float2* twx = sm;
+    float2* buf = sm + ntx;
+    for (int t = threadIdx.x; t < ntx; t += blockDim.x) twx[t] = twx_g[t];
+    const int y0 = blockIdx.y * RB;
+    const int nr = min(RB, Ny - y0);
+    float2* g = G + (size_t)blockIdx.x * Ny * Nx + (size_t)y0 * Nx;
+    const int hx = Nx / 2;
+    for (int t = threadIdx.x; t < nr * Nx; t += blockDim.x) {
+        const int r = t / Nx, qx = t - (t / Nx) * Nx;
+        int jx = qx - hx;
+        if (jx < 0) jx += Nx;
+        if (PW2) jx = brev_bits(jx, logx);
+        buf[r * Nx + jx] = g[t];
+    }
+    __syncthreads();
+    if (PW2) {
+        fft_lines_pow2<true>(buf, logx, nr, 1, Nx, twx, false);
+        for (int t = threadIdx.x; t < nr * Nx; t += blockDim.x) g[t] = buf[t];
+    } else {
+        for (int t = threadIdx.x; t < nr * Nx; t += blockDim.x) {
+            const int r = t / Nx, rx = t - (t / Nx) * Nx;
+            g[t] = dft_point<true>(buf + (size_t)r * Nx, 1, Nx, rx, twx);
+        }
+    }
+}
+
+// Pass 2: ifftshift along y and the inverse transform of P columns (blockIdx.y) of one scan
+// frequency (blockIdx.x); MODE 0 multiplies by K and writes the block's partial sum
+// part[v][blockIdx.y] (inactive v: 0), MODE 1 writes scale * G' back and folds max |.|^2.
+template <int MODE, bool PW2>
+__global__ void __launch_bounds__(kOffThreads)
+det_cols_kernel(float2* G, const float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                float2* __restrict__ part, unsigned* __restrict__ maxbits,
+                const float2* __restrict__ twy_g, int Ny, int Nx, int logy, int P, float scale) {
+    extern __shared__ float2 sm[];
+    __shared__ float2 red2[kOffThreads / 32];
+    __shared__ float redf[kOffThreads / 32];
+    const int v = blockIdx.x;
+    const int ncb = gridDim.y;
+    if (MODE == 0 && !mask[v]) {
+        if (threadIdx.x == 0) part[(size_t)v * ncb + blockIdx.y] = make_float2(0.f, 0.f);
+        return;
+    }
+    const int nty = PW2 ? Ny / 2 : Ny;
+    float2* twy = sm;
+    float2* buf = sm + nty;
+    for (int t = threadIdx.x; t < nty; t += blockDim.x) twy[t] = twy_g[t];
+    const int c0 = blockIdx.y * P;
+    const int np = min(P, Nx - c0);
+    const size_t npix = (size_t)Ny * Nx;
+    float2* g = G + (size_t)v * npix;
+    const int hy = Ny / 2;
+    for (int t = threadIdx.x; t < Ny * P; t += blockDim.x) {
+        const int i = t / P, p = t - (t / P) * P;
+        int jy = i - hy;
+        if (jy < 0) jy += Ny;
+        if (PW2) jy = brev_bits(jy, logy);
+        buf[jy * P + p] = p < np ? g[(size_t)i * Nx + c0 + p] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (PW2) fft_lines_pow2<true>(buf, logy, P, P, 1, twy, true);
+    float2 acc = make_float2(0.f, 0.f);
+    float mx = 0.f;
+    const float2* kv = K + (size_t)v * npix;
+    for (int t = threadIdx.x; t < Ny * P; t += blockDim.x) {
+        const int ry = t / P, p = t - (t / P) * P;
+        if (p >= np) continue;
+        const float2 val = PW2 ? buf[t] : dft_point<true>(buf + p, P, Ny, ry, twy);
+        const size_t e = (size_t)ry * Nx + c0 + p;
+        if (MODE == 0) {
+            const float2 k = kv[e];
+            acc.x = fmaf(val.x, k.x, fmaf(-val.y, k.y, acc.x));
+            acc.y = fmaf(val.x, k.y, fmaf(val.y, k.x, acc.y));
+        } else {
+            const float2 w = make_float2(val.x * scale, val.y * scale);
+            g[e] = w;
+            mx = fmaxf(mx, w.x * w.x + w.y * w.y);
+        }
+    }
+    if (MODE == 0) {
+        const float2 s = block_sum2(acc, red2);
+        if (threadIdx.x == 0) part[(size_t)v * ncb + blockIdx.y] = s;
+    } else {
+        const float m = block_max(mx, redf);
+        if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
+    }
+}
+
+// o_v = scale * sum_b part[v][b] in block order (inactive v: 0).
+__global__ void det_reduce_kernel(const float2* __restrict__ part, const uint8_t* __restrict__ mask,
+                                  float2* __restrict__ o, int S, int ncb, float scale) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= S) return;
+    float2 s = make_float2(0.f, 0.f);
+    if (mask[v])
+        for (int b = 0; b < ncb; ++b) {
+            const float2 a = part[(size_t)v * ncb + b];
+            s.x += a.x;
+            s.y += a.y;
+        }
+    o[v] = make_float2(s.x * scale, s.y * scale);
+}
+
+// Y_v(q) = p(q) conj p(q + q_v) on the detector grid (Algorithm 1, Eq. 2), q_v the scan-axis
+// shift turned by the scan rotation (rc, rs), evaluated in FP64 as the live plan does, stored
+// as complex64 [S][Ny][Nx].
+__global__ void probe_autocorr_kernel(float2* __restrict__ Y, const double* __restrict__ qy,
+                                      const double* __restrict__ qx, int Sx, int Ny, int Nx,
+                                      double cy, double cx, double R2, double coef, double rc,
+                                      double rs, int64_t total) {
+    const int64_t npix = (int64_t)Ny * Nx;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t / npix);
+        const int e = (int)(t - (int64_t)v * npix);
+        const int i = e / Nx, j = e - (e / Nx) * Nx;
+        const double sa = qy[v / Sx], sb = qx[v % Sx];
+        const double shy = __dsub_rn(__dmul_rn(rc, sa), __dmul_rn(rs, sb));
+        const double shx = __dadd_rn(__dmul_rn(rs, sa), __dmul_rn(rc, sb));
+        const double ky = (double)i - cy, kx = (double)j - cx;
+        const double k2 = __dadd_rn(__dmul_rn(ky, ky), __dmul_rn(kx, kx));
+        const double2 a = probe_at(k2, R2, coef);
+        float2 y = make_float2(0.f, 0.f);
+        if (a.x != 0.0 || a.y != 0.0) {
+            const double ky2 = __dadd_rn(ky, shy), kx2 = __dadd_rn(kx, shx);
+            const double k2s = __dadd_rn(__dmul_rn(ky2, ky2), __dmul_rn(kx2, kx2));
+            const double2 b = probe_at(k2s, R2, coef);
+            y = make_float2((float)(a.x * b.x + a.y * b.y), (float)(a.y * b.x - a.x * b.y));
+        }
+        Y[t] = y;
+    }
+}
+
+// K = conj(W_P) / (|W_P|^2 + eps) in place; inactive frequencies get 0.
+__global__ void wiener_kernel(float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                              int64_t npix, int64_t total, float eps) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t / npix);
+        const float2 w = K[t];
+        if (!mask[v]) {
+            K[t] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const float d = w.x * w.x + w.y * w.y + eps;
+        K[t] = make_float2(w.x / d, -w.y / d);
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------------
+
+int scan_pixels_per_cta(int n) {
+    int P = 64;
+    while (P > 4 && n * P > kScanLineElems) P >>= 1;
+    return P;
+}
+
+size_t scan_smem(int n) { return sizeof(float2) * ((size_t)n + (size_t)n * scan_pixels_per_cta(n)); }
+
+bool fused_fits(int Ny, int Nx) {
+    const int npix = Ny * Nx;
+    if (log2_exact(Ny) >= 0 && log2_exact(Nx) >= 0) return npix <= kFusedPow2Pix;
+    return npix <= kFusedDftPix;
+}
+
+size_t fused_smem(int Ny, int Nx) {
+    const bool pw2 = log2_exact(Ny) >= 0 && log2_exact(Nx) >= 0;
+    const size_t npix = (size_t)Ny * Nx;
+    return sizeof(float2) * ((pw2 ? Ny / 2 + Nx / 2 : Ny + Nx) + (pw2 ? npix : 2 * npix));
+}
+
+// Rows per CTA / columns per CTA of the two-pass detector transform (64 KB of staging).
+int rows_per_cta(int Nx) { return std::max(1, kScanLineElems / Nx); }
+int cols_per_cta(int Ny) {
+    int P = 64;
+    while (P > 1 && Ny * P > kScanLineElems) P >>= 1;
+    return P;
+}
+
+template <typename F>
+cudaError_t for_each_offline_kernel(F f) {
+    cudaError_t e = cudaSuccess;
+#define WDD_OFF_K(k) \
+    if (e == cudaSuccess) e = f(reinterpret_cast<const void*>(k))
+    WDD_OFF_K((scan_axis_kernel<uint16_t, true>));
+    WDD_OFF_K((scan_axis_kernel<uint16_t, false>));
+    WDD_OFF_K((scan_axis_kernel<float, true>));
+    WDD_OFF_K((scan_axis_kernel<float, false>));
+    WDD_OFF_K((scan_axis_kernel<double, true>));
+    WDD_OFF_K((scan_axis_kernel<double, false>));
+    WDD_OFF_K((scan_axis_kernel<float2, true>));
+    WDD_OFF_K((scan_axis_kernel<float2, false>));
+    WDD_OFF_K((det_fused_kernel<0, true>));
+    WDD_OFF_K((det_fused_kernel<0, false>));
+    WDD_OFF_K((det_fused_kernel<1, true>));
+    WDD_OFF_K((det_fused_kernel<1, false>));
+    WDD_OFF_K((det_rows_kernel<true>));
+    WDD_OFF_K((det_rows_kernel<false>));
+    WDD_OFF_K((det_cols_kernel<0, true>));
+    WDD_OFF_K((det_cols_kernel<0, false>));
+    WDD_OFF_K((det_cols_kernel<1, true>));
+    WDD_OFF_K((det_cols_kernel<1, false>));
+#undef WDD_OFF_K
+    return e;
+}
+
+cudaError_t prepare_offline_kernels() {
+    static cudaError_t status = for_each_offline_kernel(
+        [](const void* k) { return allow_max_dynamic_smem(k); });
+    return status;
+}
+
+// Forward transform along one scan axis: `outer` lines of n elements spaced es apart.
+template <typename T>
+cudaError_t launch_scan_axis(const T* src, float2* dst, const float2* tw, int n, int npix,
+                             int outer, int64_t outer_stride, int64_t es, cudaStream_t st) {
+    const int P = scan_pixels_per_cta(n);
+    const int logn = log2_exact(n);
+    dim3 grid((npix + P - 1) / P, outer);
+    const size_t smem = scan_smem(n);
+    if (logn >= 0)
+        scan_axis_kernel<T, true><<<grid, kOffThreads, smem, st>>>(src, dst, tw, n, logn, P, npix,
+                                                                   outer_stride, es);
+    else
+        scan_axis_kernel<T, false><<<grid, kOffThreads, smem, st>>>(src, dst, tw, n, logn, P, npix,
+                                                                    outer_stride, es);
+    return cudaGetLastError();
+}
+
+// Inverse detector transform of every plane of X: MODE 0 reduces against K into d_o, MODE 1
+// writes scale * the result back into X and folds its max |.|^2 into d_max.
+template <int MODE>
+cudaError_t launch_detector(const wdd_offline_plan* P, float2* X, cudaStream_t st) {
+    const int Ny = P->Ny, Nx = P->Nx;
+    const int ly = log2_exact(Ny), lx = log2_exact(Nx);
+    const float scale = (float)(1.0 / ((double)Ny * (double)Nx));
+    if (P->fused) {
+        const size_t smem = fused_smem(Ny, Nx);
+        if (ly >= 0 && lx >= 0)
+            det_fused_kernel<MODE, true><<<P->S, kDetThreads, smem, st>>>(
+                X, P->d_K, P->d_mask, P->d_o, P->d_max, P->d_tw_dy, P->d_tw_dx, Ny, Nx, ly, lx, scale);
+        else
+            det_fused_kernel<MODE, false><<<P->S, kDetThreads, smem, st>>>(
+                X, P->d_K, P->d_mask, P->d_o, P->d_max, P->d_tw_dy, P->d_tw_dx, Ny, Nx, ly, lx, scale);
+        return cudaGetLastError();
+    }
+    {
+        dim3 grid(P->S, (Ny + P->rb - 1) / P->rb);
+        const size_t smem = sizeof(float2) * ((lx >= 0 ? Nx / 2 : Nx) + (size_t)P->rb * Nx);
+        if (lx >= 0)
+            det_rows_kernel<true><<<grid, kOffThreads, smem, st>>>(X, P->d_tw_dx, Ny, Nx, lx, P->rb);
+        else
+            det_rows_kernel<false><<<grid, kOffThreads, smem, st>>>(X, P->d_tw_dx, Ny, Nx, lx, P->rb);
+    }
+    {
+        dim3 grid(P->S, P->ncb);
+        const size_t smem = sizeof(float2) * ((ly >= 0 ? Ny / 2 : Ny) + (size_t)Ny * P->cp);
+        if (ly >= 0)
+            det_cols_kernel<MODE, true><<<grid, kOffThreads, smem, st>>>(
+                X, P->d_K, P->d_mask, P->d_part, P->d_max, P->d_tw_dy, Ny, Nx, ly, P->cp, scale);
+        else
+            det_cols_kernel<MODE, false><<<grid, kOffThreads, smem, st>>>(
+                X, P->d_K, P->d_mask, P->d_part, P->d_max, P->d_tw_dy, Ny, Nx, ly, P->cp, scale);
+    }
+    if (MODE == 0)
+        det_reduce_kernel<<<(P->S + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
+            P->d_part, P->d_mask, P->d_o, P->S, P->ncb, scale);
+    return cudaGetLastError();
+}
+
+int64_t offline_planned_bytes(const wdd_offline_plan* P) {
+    const int64_t big = (int64_t)P->S * P->npix * 8;
+    int64_t b = 2 * big;
+    b += (int64_t)P->S * (1 + 8 + 8) + 8 * (int64_t)(P->Sy + P->Sx);
+    b += 8 * (int64_t)(2 * P->Sy + 2 * P->Sx + P->Ny + P->Nx);
+    if (!P->fused) b += (int64_t)P->S * P->ncb * 8;
+    return b + 4;
+}
+
+template <typename T>
+wdd_status off_alloc(wdd_offline_plan* P, T** ptr, size_t count) {
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return off_fail(WDD_ERR_OUT_OF_MEMORY, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    P->allocs.push_back({p, bytes});
+    P->device_bytes += (int64_t)bytes;
+    *ptr = static_cast<T*>(p);
+    return WDD_OK;
+}
+
+void off_release(wdd_offline_plan* P) {
+    for (auto& a : P->allocs) cudaFree(a.ptr);
+    P->allocs.clear();
+}
+
+wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, int64_t* footprint) {
+    if (!prm || !out) return off_fail(WDD_ERR_INVALID_ARG, "params or out is NULL");
+    *out = nullptr;
+    const wdd_params& p = *prm;
+    if (p.scan_y <= 0 || p.scan_x <= 0 || p.det_y <= 0 || p.det_x <= 0)
+        return off_fail(WDD_ERR_INVALID_ARG, "scan and detector sizes must be positive");
+    if (p.scan_y > 4096 || p.scan_x > 4096)
+        return off_fail(WDD_ERR_UNSUPPORTED, "scan side above 4096");
+    if (p.det_y > 1024 || p.det_x > 1024)
+        return off_fail(WDD_ERR_UNSUPPORTED, "detector side above 1024");
+    if (!(p.scan_step_m > 0) || !(p.det_px_inv_m > 0) || !(p.voltage_v > 0) ||
+        !(p.semiconv_rad > 0) || !std::isfinite(p.defocus_m))
+        return off_fail(WDD_ERR_INVALID_ARG, "step, sampling, voltage and angle must be positive");
+    if (!(p.epsilon >= 0) || !std::isfinite(p.epsilon))
+        return off_fail(WDD_ERR_INVALID_ARG, "epsilon must be finite and non-negative");
+    if (p.frame_dtype < WDD_FRAME_U16 || p.frame_dtype > WDD_FRAME_F64)
+        return off_fail(WDD_ERR_INVALID_ARG, "unknown frame dtype");
+    if (!std::isfinite(p.scan_rotation_rad))
+        return off_fail(WDD_ERR_INVALID_ARG, "scan_rotation_rad must be finite");
+    const bool cy_default = p.det_center_y < 0 || p.det_center_y == (double)(p.det_y / 2);
+    const bool cx_default = p.det_center_x < 0 || p.det_center_x == (double)(p.det_x / 2);
+    if (!cy_default || !cx_default)
+        return off_fail(WDD_ERR_UNSUPPORTED,
+                        "classical WDD moves the zero frequency by an integer roll: the detector "
+                        "centre must be det / 2");
+
+    wdd_offline_plan* P = new wdd_offline_plan();
+    P->p = p;
+    P->Sy = p.scan_y;
+    P->Sx = p.scan_x;
+    P->S = p.scan_y * p.scan_x;
+    P->Ny = p.det_y;
+    P->Nx = p.det_x;
+    P->npix = p.det_y * p.det_x;
+    P->fused = fused_fits(P->Ny, P->Nx) ? 1 : 0;
+    P->rb = rows_per_cta(P->Nx);
+    P->cp = cols_per_cta(P->Ny);
+    P->ncb = (P->Nx + P->cp - 1) / P->cp;
+    P->lambda = electron_wavelength(p.voltage_v);
+    P->R = p.semiconv_rad / (P->lambda * p.det_px_inv_m);
+    std::vector<double> qy, qx;
+    std::vector<uint8_t> mask;
+    P->n_active = scan_geometry(p, P->R, qy, qx, mask);
+
+    const int64_t need = offline_planned_bytes(P);
+    if (footprint) {
+        *footprint = need;
+        delete P;
+        return WDD_OK;
+    }
+    if (p.hbm_budget_bytes > 0 && need > p.hbm_budget_bytes) {
+        delete P;
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "classical plan needs %lld bytes, budget is %lld",
+                      (long long)need, (long long)p.hbm_budget_bytes);
+        return off_fail(WDD_ERR_OUT_OF_MEMORY, buf);
+    }
+    {
+        cudaError_t pe = prepare_offline_kernels();
+        if (pe == cudaSuccess) pe = prepare_kernels();
+        if (pe != cudaSuccess) {
+            delete P;
+            return off_cuda_fail(pe, "kernel attributes");
+        }
+    }
+    wdd_status sst = WDD_OK;
+#define WDD_OFF_ALLOC(ptr, n)                                           \
+    do {                                                                \
+        sst = off_alloc(P, &(ptr), (n));                                \
+        if (sst != WDD_OK) { off_release(P); delete P; return sst; }    \
+    } while (0)
+    const size_t big = (size_t)P->S * P->npix;
+    WDD_OFF_ALLOC(P->d_G, big);
+    WDD_OFF_ALLOC(P->d_K, big);
+    WDD_OFF_ALLOC(P->d_mask, P->S);
+    WDD_OFF_ALLOC(P->d_qy, P->Sy);
+    WDD_OFF_ALLOC(P->d_qx, P->Sx);
+    WDD_OFF_ALLOC(P->d_tw_sy, P->Sy);
+    WDD_OFF_ALLOC(P->d_tw_sx, P->Sx);
+    WDD_OFF_ALLOC(P->d_tw_dy, P->Ny);
+    WDD_OFF_ALLOC(P->d_tw_dx, P->Nx);
+    WDD_OFF_ALLOC(P->d_twy_inv, P->Sy);
+    WDD_OFF_ALLOC(P->d_twx_inv, P->Sx);
+    WDD_OFF_ALLOC(P->d_o, P->S);
+    WDD_OFF_ALLOC(P->d_tmp, P->S);
+    WDD_OFF_ALLOC(P->d_max, 1);
+    if (!P->fused) WDD_OFF_ALLOC(P->d_part, (size_t)P->S * P->ncb);
+#undef WDD_OFF_ALLOC
+
+    cudaStream_t s0 = nullptr;
+    auto cbail = [&](cudaError_t e, const char* w) {
+        off_cuda_fail(e, w);
+        off_release(P);
+        delete P;
+        return WDD_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMemcpy(P->d_qy, qy.data(), 8 * P->Sy, cudaMemcpyHostToDevice))) return cbail(e, "copy shifts");
+    if ((e = cudaMemcpy(P->d_qx, qx.data(), 8 * P->Sx, cudaMemcpyHostToDevice))) return cbail(e, "copy shifts");
+    if ((e = cudaMemcpy(P->d_mask, mask.data(), P->S, cudaMemcpyHostToDevice))) return cbail(e, "copy mask");
+    auto tw = [&](float2* d, int n) {
+        twiddle_kernel<<<(n + kOffThreads - 1) / kOffThreads, kOffThreads, 0, s0>>>(d, n);
+    };
+    tw(P->d_tw_sy, P->Sy);
+    tw(P->d_tw_sx, P->Sx);
+    tw(P->d_tw_dy, P->Ny);
+    tw(P->d_tw_dx, P->Nx);
+    if ((e = launch_idft_tables(P->d_twy_inv, P->Sy, P->d_twx_inv, P->Sx, s0))) return cbail(e, "tables");
+
+    // ---- Wiener kernel: Y_v, W_P = IFFT2(ifftshift Y_v), eps_eff, conj(W_P) / (|W_P|^2 + eps) ----
+    const double R2 = P->R * P->R;
+    const double coef = 3.14159265358979323846 * P->lambda * p.defocus_m *
+                        (p.det_px_inv_m * p.det_px_inv_m);
+    const double rc = std::cos(p.scan_rotation_rad), rs = std::sin(p.scan_rotation_rad);
+    const int64_t total = (int64_t)big;
+    const int ew_blocks = (int)std::min<int64_t>((total + kOffThreads - 1) / kOffThreads, 152 * 64);
+    probe_autocorr_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(
+        P->d_K, P->d_qy, P->d_qx, P->Sx, P->Ny, P->Nx, (double)(P->Ny / 2), (double)(P->Nx / 2),
+        R2, coef, rc, rs, total);
+    if ((e = cudaGetLastError())) return cbail(e, "probe autocorrelation");
+    if ((e = cudaMemset(P->d_max, 0, 4))) return cbail(e, "zero max");
+    if ((e = launch_detector<1>(P, P->d_K, s0))) return cbail(e, "probe transform");
+    unsigned maxbits = 0;
+    if ((e = cudaMemcpy(&maxbits, P->d_max, 4, cudaMemcpyDeviceToHost))) return cbail(e, "max");
+    float maxwp;
+    std::memcpy(&maxwp, &maxbits, 4);
+    P->eps_eff = p.eps_absolute ? p.epsilon : p.epsilon * (double)maxwp;
+    if (!(P->eps_eff > 0) && p.epsilon > 0) {
+        off_release(P);
+        delete P;
+        return off_fail(WDD_ERR_INVALID_ARG, "probe autocorrelation is zero everywhere");
+    }
+    wiener_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(P->d_K, P->d_mask, P->npix, total,
+                                                     (float)P->eps_eff);
+    if ((e = cudaGetLastError())) return cbail(e, "Wiener kernel");
+    if ((e = cudaDeviceSynchronize())) return cbail(e, "classical plan build");
+    *out = P;
+    return WDD_OK;
+}
+
+}  // namespace
+}  // namespace wdd
+
+using namespace wdd;
+
+wdd_status wdd_offline_plan_create(const wdd_params* p, wdd_offline_plan** out) {
+    return offline_create_impl(p, out, nullptr);
+}
+
+wdd_status wdd_offline_footprint(const wdd_params* p, int64_t* bytes) {
+    if (!bytes) return off_fail(WDD_ERR_INVALID_ARG, "bytes is NULL");
+    wdd_offline_plan* unused = nullptr;
+    return offline_create_impl(p, &unused, bytes);
+}
+
+wdd_status wdd_offline_plan_destroy(wdd_offline_plan* P) {
+    if (!P) return off_fail(WDD_ERR_INVALID_ARG, "plan is NULL");
+    cudaDeviceSynchronize();
+    off_release(P);
+    delete P;
+    return WDD_OK;
+}
+
+wdd_status wdd_offline_reconstruct(wdd_offline_plan* P, const void* frames, wdd_result* out,
+                                   wdd_stream_t stream) {
+    if (!P || !frames || !out || !out->obj)
+        return off_fail(WDD_ERR_INVALID_ARG, "plan, frames, out and out->obj must not be NULL");
+    cudaPointerAttributes attr{};
+    cudaError_t e = cudaPointerGetAttributes(&attr, frames);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    const void* src = nullptr;
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+        src = frames;
+    else if (attr.type == cudaMemoryTypeHost)
+        src = attr.devicePointer ? attr.devicePointer : frames;
+    else
+        return off_fail(WDD_ERR_INVALID_ARG, "frames must be in device or pinned host memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int npix = P->npix;
+    const int64_t sx_stride = (int64_t)P->Sx * npix;
+    // Eq. 2: forward transform over s_x (from the frames), then over s_y (in place)
+    switch (P->p.frame_dtype) {
+        case WDD_FRAME_U16:
+            e = launch_scan_axis(static_cast<const uint16_t*>(src), P->d_G, P->d_tw_sx, P->Sx, npix,
+                                 P->Sy, sx_stride, npix, st);
+            break;
+        case WDD_FRAME_F32:
+            e = launch_scan_axis(static_cast<const float*>(src), P->d_G, P->d_tw_sx, P->Sx, npix,
+                                 P->Sy, sx_stride, npix, st);
+            break;
+        default:
+            e = launch_scan_axis(static_cast<const double*>(src), P->d_G, P->d_tw_sx, P->Sx, npix,
+                                 P->Sy, sx_stride, npix, st);
+            break;
+    }
+    if (e == cudaSuccess)
+        e = launch_scan_axis(static_cast<const float2*>(P->d_G), P->d_G, P->d_tw_sy, P->Sy, npix,
+                             P->Sx, npix, sx_stride, st);
+    // Eq. 2-3: detector transform, Wiener product and the sum over r
+    if (e == cudaSuccess) e = launch_detector<0>(P, P->d_G, st);
+    // Eq. 3: normalisation, conjugated inverse DFT over the scan
+    if (e == cudaSuccess)
+        e = launch_idft(P->d_o, P->d_twx_inv, P->d_twy_inv, P->d_tmp, P->Sy, P->Sx,
+                        static_cast<float2*>(out->obj), out->phase, st);
+    if (e != cudaSuccess) return off_cuda_fail(e, "classical reconstruction");
+    out->frames_seen = P->S;
+    out->positions_covered = P->S;
+    return WDD_OK;
+}
+
+wdd_status wdd_offline_copy_array(wdd_offline_plan* P, int32_t which, void* dst, int64_t bytes,
+                                  int64_t* written) {
+    if (!P || !dst) return off_fail(WDD_ERR_INVALID_ARG, "plan or destination is NULL");
+    const void* src = nullptr;
+    size_t size = 0;
+    switch (which) {
+        case WDD_OFFLINE_SPECTRUM: src = P->d_o; size = 8 * (size_t)P->S; break;
+        case WDD_OFFLINE_WIENER: src = P->d_K; size = 8 * (size_t)P->S * P->npix; break;
+        case WDD_OFFLINE_MASK: src = P->d_mask; size = (size_t)P->S; break;
+        default: return off_fail(WDD_ERR_INVALID_ARG, "unknown array");
+    }
+    if (bytes < (int64_t)size) return off_fail(WDD_ERR_INVALID_ARG, "destination too small");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, size, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return off_cuda_fail(e, "copy");
+    if (written) *written = (int64_t)size;
+    return WDD_OK;
+}
+
+wdd_status wdd_offline_get_info(const wdd_offline_plan* P, int64_t* device_bytes,
+                                int32_t* n_active, int32_t* fused, double* eps_eff) {
+    if (!P) return off_fail(WDD_ERR_INVALID_ARG, "plan is NULL");
+    if (device_bytes) *device_bytes = P->device_bytes;
+    if (n_active) *n_active = P->n_active;
+    if (fused) *fused = P->fused;
+    if (eps_eff) *eps_eff = P->eps_eff;
+    return WDD_OK;
+}

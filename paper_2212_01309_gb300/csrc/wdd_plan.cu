@@ -10,6 +10,7 @@
 
 #include <cmath>
 
+#include "wdd_device.cuh"
 #include "wdd_internal.h"
 
 namespace wdd {
@@ -76,16 +77,6 @@ __global__ void fourier_basis_kernel(double2* B, int n, double center) {
 }
 
 constexpr int kChiRows = 8;
-
-// Probe spectrum at a detector point k (pixels) given its squared radius k2 (already rounded):
-// A(k) exp(-i coef k2) with A the hard-edged aperture |k|^2 <= R^2.
-__device__ __forceinline__ double2 probe_at(double k2, double R2, double coef) {
-    if (!(k2 <= R2)) return make_double2(0.0, 0.0);
-    if (coef == 0.0) return make_double2(1.0, 0.0);
-    double s, c;
-    sincos(__dmul_rn(coef, k2), &s, &c);
-    return make_double2(c, -s);
-}
 
 // chi_v = By^T Y_v Bx for one scan frequency v per block, Y_v(q) = p(q) conj p(q + q_v)
 // (Algorithm 1), with q_v the scan-axis shift (qy, qx) turned by the scan rotation (rc, rs):

@@ -197,6 +197,19 @@ cudaError_t prepare_reconstruct_kernels() {
     return e;
 }
 
+cudaError_t launch_idft_tables(float2* twy, int Sy, float2* twx, int Sx, cudaStream_t st) {
+    const int nt = Sy > Sx ? Sy : Sx;
+    idft_tables_kernel<<<(nt + kThreads - 1) / kThreads, kThreads, 0, st>>>(twy, Sy, twx, Sx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_idft(const float2* o, const float2* twx, const float2* twy, float2* tmp, int Sy,
+                        int Sx, float2* obj, float* phase, cudaStream_t st) {
+    idft_rows_kernel<<<Sy, kThreads, 2 * sizeof(float2) * Sx, st>>>(o, twx, tmp, Sy, Sx);
+    idft_cols_kernel<<<Sx, kThreads, 2 * sizeof(float2) * Sy, st>>>(tmp, twy, obj, phase, Sy, Sx);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st) {
     idft_rows_kernel<<<P->Sy, kThreads, 2 * sizeof(float2) * P->Sx, st>>>(P->d_o, P->d_twx,
                                                                          P->d_tmp, P->Sy, P->Sx);

@@ -108,6 +108,19 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
                                            ctypes.c_int32, ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "wdd_offline_plan_create": (ctypes.c_int, [ctypes.POINTER(Params),
+                                               ctypes.POINTER(ctypes.c_void_p)]),
+    "wdd_offline_footprint": (ctypes.c_int, [ctypes.POINTER(Params),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "wdd_offline_reconstruct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(Result), ctypes.c_void_p]),
+    "wdd_offline_copy_array": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "wdd_offline_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "wdd_offline_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_get_hit_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wdd_copy_array": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -348,6 +361,84 @@ class Plan:
 def selftest_bounded_wait(wait_ns: int = 50_000_000) -> int:
     """Runs the device bounded-wait self test; returns the status code (ERR_TIMEOUT expected)."""
     return int(lib().wdd_selftest_bounded_wait(int(wait_ns)))
+
+
+def offline_footprint(params: Params) -> int:
+    b = ctypes.c_int64()
+    _check(lib().wdd_offline_footprint(ctypes.byref(params), ctypes.byref(b)),
+           "wdd_offline_footprint")
+    return int(b.value)
+
+
+class OfflinePlan:
+    """Classical WDD on the whole 4-D dataset (wdd_offline_*): the comparison method, on the GPU."""
+
+    def __init__(self, params: Params):
+        import torch  # noqa: F401  (device context, memory and streams)
+        self.params = params
+        h = ctypes.c_void_p()
+        _check(lib().wdd_offline_plan_create(ctypes.byref(params), ctypes.byref(h)),
+               "wdd_offline_plan_create")
+        self._h = h
+        self.S = params.scan_y * params.scan_x
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().wdd_offline_plan_destroy(self._h), "wdd_offline_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reconstruct(self, frames, obj=None, phase=None, stream=None):
+        """frames: [S, det_y, det_x] torch tensor on the GPU or in pinned memory, raster order.
+        Returns (object complex64 [S_y, S_x], phase f32)."""
+        import torch
+        if hasattr(frames, "is_contiguous") and not frames.is_contiguous():
+            raise ValueError("frames must be contiguous")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        shape = (self.params.scan_y, self.params.scan_x)
+        if obj is None:
+            obj = torch.empty(shape, dtype=torch.complex64, device=dev)
+        if phase is None:
+            phase = torch.empty(shape, dtype=torch.float32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        r = Result(obj=_ptr(obj), phase=_ptr(phase) if phase is not False else None)
+        _check(lib().wdd_offline_reconstruct(self._h, ctypes.c_void_p(_ptr(frames)),
+                                             ctypes.byref(r),
+                                             ctypes.c_void_p(int(stream.cuda_stream))),
+               "wdd_offline_reconstruct")
+        return obj, (phase if phase is not False else None)
+
+    def info(self) -> dict:
+        b, n, f, e = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().wdd_offline_get_info(self._h, ctypes.byref(b), ctypes.byref(n),
+                                          ctypes.byref(f), ctypes.byref(e)),
+               "wdd_offline_get_info")
+        return {"device_bytes": b.value, "n_active": n.value, "fused": f.value,
+                "eps_eff": e.value}
+
+    def copy_array(self, which: str) -> np.ndarray:
+        p = self.params
+        shapes = {"spectrum": (0, np.complex64, (self.S,)),
+                  "wiener": (1, np.complex64, (self.S, p.det_y, p.det_x)),
+                  "mask": (2, np.uint8, (self.S,))}
+        code, dt, shape = shapes[which]
+        out = np.empty(shape, dtype=dt)
+        w = ctypes.c_int64()
+        _check(lib().wdd_offline_copy_array(self._h, code, ctypes.c_void_p(out.ctypes.data),
+                                            out.nbytes, ctypes.byref(w)), "wdd_offline_copy_array")
+        return out
 
 
 def detector_center(frames, stream=None) -> tuple[float, float]:

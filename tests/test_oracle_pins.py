@@ -217,6 +217,39 @@ def test_live_equals_offline_full_scan():
         assert W.complex_rel_l2(o_live, o_off) < 1e-10
 
 
+def test_offline_per_frequency_equals_fft_route():
+    """Classical WDD one frequency at a time (plain scan sum) equals the FFT route (Eq. 2-3), for
+    active and inactive frequencies, with and without a scan rotation."""
+    acq = c1_odd(defocus_m=4e-9)
+    F = synth.all_frames(acq)
+    idx = synth.raster_indices(acq)
+    for rot in (0.0, 0.6):
+        p = dataclasses.replace(params(acq), scan_rotation_rad=rot, epsilon=1e-2)
+        o = W.offline_wdd(F, p)
+        WP = np.stack([W.offline_probe_wigner(p, vy, vx) for vy in range(p.scan_y)
+                       for vx in range(p.scan_x)])
+        eps = p.epsilon * float(np.max(np.abs(WP) ** 2))
+        for vy, vx in [(0, 0), (1, 0), (0, 3), (acq.scan_y - 1, 2), (4, acq.scan_x - 1)]:
+            got = W.offline_wdd_frequency(F, idx, p, vy, vx, eps)
+            ref = o[vy * p.scan_x + vx]
+            assert abs(got - ref) <= 1e-11 * np.abs(o).max()
+
+
+def test_offline_probe_wigner_peak_closed_form():
+    """With an aperture of amplitude 1, |W_P(v, r)| <= (1/N^2) sum_q A(q) A(q + q_v) <= n_A / N^2,
+    reached at v = 0, r = 0: max |W_P|^2 = (n_A / N^2)^2 with n_A the aperture pixel count."""
+    acq = c1_odd(defocus_m=7e-9)
+    p = params(acq)
+    R = W.bright_field_radius_px(p)
+    qy = np.arange(p.det_y) - p.cy
+    qx = np.arange(p.det_x) - p.cx
+    n_a = int(np.sum(qy[:, None] ** 2 + qx[None, :] ** 2 <= R * R))
+    peak = max(float(np.max(np.abs(W.offline_probe_wigner(p, vy, vx)) ** 2))
+               for vy in range(p.scan_y) for vx in range(p.scan_x))
+    assert abs(peak - (n_a / (p.det_y * p.det_x)) ** 2) < 1e-14
+    assert abs(W.offline_probe_wigner(p, 0, 0)[0, 0] - n_a / (p.det_y * p.det_x)) < 1e-14
+
+
 def test_per_frame_equals_batched():
     """Algorithm 2 frame by frame equals the matrix form F_2D C (check 2)."""
     acq, _ = synth.config("c1")
