@@ -465,6 +465,191 @@ __global__ void wiener_kernel(float2* __restrict__ K, const uint8_t* __restrict_
     }
 }
 
+// ---- four-step transforms: a 1-D transform of n = N1 N2 points as N2 register DFTs of N1
+// points, a twiddle w_n^(j2 k1), and N1 register DFTs of N2 points, with one shared-memory round
+// trip in between (X[k1 + N1 k2] = sum_j2 w_N2^(j2 k2) w_n^(j2 k1) sum_j1 w_N1^(j1 k1) x[j1 N2 + j2]).
+
+// In-register DFT of M = 2^m points, natural order in and out (radix-2 decimation in time after a
+// compile-time bit reversal); w_M^t = tw[t * tws] from the table tw[j] = exp(-2 pi i j / n),
+// tws = n / M; INV conjugates the twiddles.
+template <int M, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&x)[M], const float2* tw, int tws) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 1, t = i; b < M; b <<= 1, t >>= 1) r = (r << 1) | (t & 1);
+        if (r > i) {
+            const float2 t = x[i];
+            x[i] = x[r];
+            x[r] = t;
+        }
+    }
+#pragma unroll
+    for (int h = 1; h < M; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            float2 w = tw[k * (M / (2 * h)) * tws];
+            if (INV) w.y = -w.y;
+#pragma unroll
+            for (int i0 = k; i0 < M; i0 += 2 * h) {
+                const float2 a = x[i0];
+                const float2 c = k == 0 ? x[i0 + h] : cmulf(w, x[i0 + h]);
+                x[i0] = make_float2(a.x + c.x, a.y + c.y);
+                x[i0 + h] = make_float2(a.x - c.x, a.y - c.y);
+            }
+        }
+    }
+}
+
+// Forward transform of n = N1 N2 points along one scan axis for a block of P pixels (same
+// addressing as scan_axis_kernel).  Step 1 reads its N1 points straight from global memory.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(kOffThreads)
+scan_axis4_kernel(const T* src, float2* dst, const float2* __restrict__ tw_g, int P, int npix,
+                  int64_t outer_stride, int64_t es) {
+    constexpr int n = N1 * N2;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;        // n
+    float2* buf = sm + n;   // [k1][j2][P]
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = tw_g[t];
+    __syncthreads();
+    const int q0 = blockIdx.x * P;
+    const int np = min(P, npix - q0);
+    const int64_t base = (int64_t)blockIdx.y * outer_stride + q0;
+    for (int task = threadIdx.x; task < N2 * P; task += blockDim.x) {
+        const int j2 = task / P, p = task - (task / P) * P;
+        float2 x[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1)
+            x[j1] = p < np ? as_c(src[base + (int64_t)(j1 * N2 + j2) * es + p])
+                           : make_float2(0.f, 0.f);
+        dft_reg<N1, false>(x, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            const float2 y = (k1 == 0 || j2 == 0) ? x[k1] : cmulf(x[k1], tw[j2 * k1]);
+            buf[(k1 * N2 + j2) * P + p] = y;
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < N1 * P; task += blockDim.x) {
+        const int k1 = task / P, p = task - (task / P) * P;
+        float2 y[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) y[j2] = buf[(k1 * N2 + j2) * P + p];
+        dft_reg<N2, false>(y, tw, N1);
+        if (p < np) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) dst[base + (int64_t)(k1 + N1 * k2) * es + p] = y[k2];
+        }
+    }
+}
+
+// Square detector planes of N = N1 N2 pixels (one scan frequency per CTA), four-step: columns
+// first, straight from global memory with the ifftshift of both axes folded into the loads, then
+// rows, every step in place in a padded plane (row stride N + N/16 + 1, a pad every 16 entries:
+// conflict-free for the access orders below).  After the column steps, plane row q holds output
+// row ry = q / N2 + N1 (q % N2); the row steps produce output column rx = k1 + N1 k2 directly,
+// so the Wiener kernel is read in order.  MODE as in det_fused_kernel.
+template <int MODE, int N1, int N2>
+__global__ void __launch_bounds__(kDetThreads)
+det_fused4_kernel(float2* G, const float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                  float2* __restrict__ o, unsigned* __restrict__ maxbits,
+                  const float2* __restrict__ tw_g, float scale) {
+    constexpr int N = N1 * N2;
+    constexpr int RS = N + N / 16 + 1;
+    extern __shared__ float2 sm[];
+    __shared__ float2 red2[kDetThreads / 32];
+    __shared__ float redf[kDetThreads / 32];
+    float2* tw = sm;        // N
+    float2* A = sm + N;     // N * RS
+    const int v = blockIdx.x;
+    if (MODE == 0 && !mask[v]) {
+        if (threadIdx.x == 0) o[v] = make_float2(0.f, 0.f);
+        return;
+    }
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = tw_g[t];
+    __syncthreads();
+    float2* g = G + (size_t)v * N * N;
+    auto pos = [](int row, int e) { return row * RS + e + (e >> 4); };
+    constexpr int H = N / 2;
+    // columns, step 1: shifted row j = j1 N2 + j2 is stored row (j + N/2) mod N
+    for (int task = threadIdx.x; task < N * N2; task += blockDim.x) {
+        const int c = task % N, j2 = task / N;
+        const int col = (c + H) & (N - 1);
+        float2 x[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) x[j1] = g[(size_t)(((j1 * N2 + j2) + H) & (N - 1)) * N + col];
+        dft_reg<N1, true>(x, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 w = tw[j2 * k1];
+            w.y = -w.y;
+            A[pos(k1 * N2 + j2, c)] = (k1 == 0 || j2 == 0) ? x[k1] : cmulf(x[k1], w);
+        }
+    }
+    __syncthreads();
+    // columns, step 2 (in place: reads and writes plane rows k1 N2 + 0 .. N2 - 1)
+    for (int task = threadIdx.x; task < N * N1; task += blockDim.x) {
+        const int c = task % N, k1 = task / N;
+        float2 y[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) y[j2] = A[pos(k1 * N2 + j2, c)];
+        dft_reg<N2, true>(y, tw, N1);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) A[pos(k1 * N2 + k2, c)] = y[k2];
+    }
+    __syncthreads();
+    // rows, step 1 (in place: entries j1 N2 + j2 of plane row q)
+    for (int task = threadIdx.x; task < N * N2; task += blockDim.x) {
+        const int q = task % N, j2 = task / N;
+        float2 x[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) x[j1] = A[pos(q, j1 * N2 + j2)];
+        dft_reg<N1, true>(x, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 w = tw[j2 * k1];
+            w.y = -w.y;
+            A[pos(q, k1 * N2 + j2)] = (k1 == 0 || j2 == 0) ? x[k1] : cmulf(x[k1], w);
+        }
+    }
+    __syncthreads();
+    // rows, step 2, consumed directly
+    float2 acc = make_float2(0.f, 0.f);
+    float mx = 0.f;
+    const float2* kv = K + (size_t)v * N * N;
+    for (int task = threadIdx.x; task < N * N1; task += blockDim.x) {
+        const int k1 = task % N1, q = task / N1;
+        float2 y[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) y[j2] = A[pos(q, k1 * N2 + j2)];
+        dft_reg<N2, true>(y, tw, N1);
+        const int ry = q / N2 + N1 * (q % N2);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const size_t e = (size_t)ry * N + k1 + N1 * k2;
+            const float2 val = y[k2];
+            if (MODE == 0) {
+                const float2 k = kv[e];
+                acc.x = fmaf(val.x, k.x, fmaf(-val.y, k.y, acc.x));
+                acc.y = fmaf(val.x, k.y, fmaf(val.y, k.x, acc.y));
+            } else {
+                const float2 w = make_float2(val.x * scale, val.y * scale);
+                g[e] = w;
+                mx = fmaxf(mx, w.x * w.x + w.y * w.y);
+            }
+        }
+    }
+    if (MODE == 0) {
+        const float2 s = block_sum2(acc, red2);
+        if (threadIdx.x == 0) o[v] = make_float2(s.x * scale, s.y * scale);
+    } else {
+        const float m = block_max(mx, redf);
+        if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
+    }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 
 int scan_pixels_per_cta(int n) {
@@ -495,11 +680,41 @@ int cols_per_cta(int Ny) {
     return P;
 }
 
+// Sizes with a four-step transform: n = N1 N2 with register DFTs of at most 32 points.
+#define WDD_FOUR_STEP_SIZES(X) X(32, 8, 4) X(64, 8, 8) X(128, 16, 8) X(256, 16, 16) \
+    X(512, 32, 16) X(1024, 32, 32)
+#define WDD_DET4_SIZES(X) X(32, 8, 4) X(64, 8, 8) X(128, 16, 8)
+
+bool four_step_len(int n) {
+#define WDD_FS_CASE(nn, a, b) if (n == nn) return true;
+    WDD_FOUR_STEP_SIZES(WDD_FS_CASE)
+#undef WDD_FS_CASE
+    return false;
+}
+bool det4_square(int Ny, int Nx) { return Ny == Nx && (Nx == 32 || Nx == 64 || Nx == 128); }
+int scan4_pixels_per_cta(int n) { return std::min(64, std::max(8, kScanLineElems / n)); }
+size_t scan4_smem(int n) {
+    return sizeof(float2) * ((size_t)n + (size_t)n * scan4_pixels_per_cta(n));
+}
+size_t det4_smem(int N) { return sizeof(float2) * ((size_t)N + (size_t)N * (N + N / 16 + 1)); }
+
 template <typename F>
 cudaError_t for_each_offline_kernel(F f) {
     cudaError_t e = cudaSuccess;
 #define WDD_OFF_K(k) \
     if (e == cudaSuccess) e = f(reinterpret_cast<const void*>(k))
+#define WDD_OFF_K4(nn, a, b)                                   \
+    WDD_OFF_K((scan_axis4_kernel<uint16_t, a, b>));            \
+    WDD_OFF_K((scan_axis4_kernel<float, a, b>));               \
+    WDD_OFF_K((scan_axis4_kernel<double, a, b>));              \
+    WDD_OFF_K((scan_axis4_kernel<float2, a, b>));
+    WDD_FOUR_STEP_SIZES(WDD_OFF_K4)
+#undef WDD_OFF_K4
+#define WDD_OFF_D4(nn, a, b)                                   \
+    WDD_OFF_K((det_fused4_kernel<0, a, b>));                   \
+    WDD_OFF_K((det_fused4_kernel<1, a, b>));
+    WDD_DET4_SIZES(WDD_OFF_D4)
+#undef WDD_OFF_D4
     WDD_OFF_K((scan_axis_kernel<uint16_t, true>));
     WDD_OFF_K((scan_axis_kernel<uint16_t, false>));
     WDD_OFF_K((scan_axis_kernel<float, true>));
@@ -532,6 +747,18 @@ cudaError_t prepare_offline_kernels() {
 template <typename T>
 cudaError_t launch_scan_axis(const T* src, float2* dst, const float2* tw, int n, int npix,
                              int outer, int64_t outer_stride, int64_t es, cudaStream_t st) {
+    if (four_step_len(n)) {
+        const int P = scan4_pixels_per_cta(n);
+        dim3 grid((npix + P - 1) / P, outer);
+        const size_t smem = scan4_smem(n);
+#define WDD_SCAN4(nn, a, b)                                                                  \
+        if (n == nn)                                                                         \
+            scan_axis4_kernel<T, a, b><<<grid, kOffThreads, smem, st>>>(src, dst, tw, P, npix, \
+                                                                        outer_stride, es);
+        WDD_FOUR_STEP_SIZES(WDD_SCAN4)
+#undef WDD_SCAN4
+        return cudaGetLastError();
+    }
     const int P = scan_pixels_per_cta(n);
     const int logn = log2_exact(n);
     dim3 grid((npix + P - 1) / P, outer);
@@ -552,6 +779,16 @@ cudaError_t launch_detector(const wdd_offline_plan* P, float2* X, cudaStream_t s
     const int Ny = P->Ny, Nx = P->Nx;
     const int ly = log2_exact(Ny), lx = log2_exact(Nx);
     const float scale = (float)(1.0 / ((double)Ny * (double)Nx));
+    if (det4_square(Ny, Nx)) {
+        const size_t smem = det4_smem(Nx);
+#define WDD_DET4(nn, a, b)                                                                     \
+        if (Nx == nn)                                                                          \
+            det_fused4_kernel<MODE, a, b><<<P->S, kDetThreads, smem, st>>>(                    \
+                X, P->d_K, P->d_mask, P->d_o, P->d_max, P->d_tw_dx, scale);
+        WDD_DET4_SIZES(WDD_DET4)
+#undef WDD_DET4
+        return cudaGetLastError();
+    }
     if (P->fused) {
         const size_t smem = fused_smem(Ny, Nx);
         if (ly >= 0 && lx >= 0)
@@ -649,7 +886,7 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
     P->Ny = p.det_y;
     P->Nx = p.det_x;
     P->npix = p.det_y * p.det_x;
-    P->fused = fused_fits(P->Ny, P->Nx) ? 1 : 0;
+    P->fused = (fused_fits(P->Ny, P->Nx) || det4_square(P->Ny, P->Nx)) ? 1 : 0;
     P->rb = rows_per_cta(P->Nx);
     P->cp = cols_per_cta(P->Ny);
     P->ncb = (P->Nx + P->cp - 1) / P->cp;
