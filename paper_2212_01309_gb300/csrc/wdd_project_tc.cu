@@ -193,8 +193,10 @@ __device__ __forceinline__ void tile_rows_direct(uint32_t taddr, float inv, floa
     }
 }
 
+// Four CTAs per SM (64 registers): more CTAs in flight hide the per-item load latency better
+// than staging whole frames in shared memory, which leaves room for only two.
 template <typename FT>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 4)
 project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
     extern __shared__ __align__(128) uint8_t sm[];
     const int tiles = (a.Ny + kTM - 1) / kTM;
