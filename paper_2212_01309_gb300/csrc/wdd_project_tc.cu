@@ -31,6 +31,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "wdd_device.cuh"
 #include "wdd_internal.h"
 
@@ -155,14 +157,41 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Loads this thread's part of item `it` = (tile it / chunks, chunk it % chunks): for unit
-// v = warp + 8 u, row 8 (v % 16) + r of the tile and columns 32 (v / 16) + 8 q .. + 7 of the
-// chunk; zeros outside the frame.
+// Loads this thread's part of item `it` = (tile it / chunks, chunk it % chunks); zeros outside
+// the frame.  uint16 frames: for unit v = warp + 8 u, row 8 (v % 16) + r of the tile and columns
+// 32 (v / 16) + 8 q .. + 7 of the chunk (one 16-byte load; a warp reads 64 contiguous bytes of
+// each of 8 rows).  float32 frames: row 8 (v % 16) + (lane >> 2) and columns 4 (lane & 3) .. + 3
+// and 16 + 4 (lane & 3) .. + 3 (two 16-byte loads, each reading 64 contiguous bytes of 8 rows:
+// whole 32-byte sectors per instruction).
 template <typename FT>
 __device__ __forceinline__ void load_item(const FT* frame, int it, int n_items, int chunks, int Ny,
                                           int Nx, int warp, int r, int q, float (&dst)[kU][8]) {
     const int mt = it / chunks, kc = it % chunks;
     const int w = min(kTK, Nx - kc * kTK);   // a multiple of 16
+    if constexpr (std::is_same<FT, float>::value) {
+        const int lane = r + 8 * q;
+        const int rr = lane >> 2, c4 = 4 * (lane & 3);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int v = warp + 8 * u;
+            const int row = mt * kTM + 8 * (v & 15) + rr;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = 16 * h + c4;
+                if (it < n_items && col < w && row < Ny) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(
+                        frame + (size_t)row * Nx + kc * kTK + col));
+                    dst[u][4 * h] = a.x;
+                    dst[u][4 * h + 1] = a.y;
+                    dst[u][4 * h + 2] = a.z;
+                    dst[u][4 * h + 3] = a.w;
+                } else {
+                    dst[u][4 * h] = dst[u][4 * h + 1] = dst[u][4 * h + 2] = dst[u][4 * h + 3] = 0.f;
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
         const int v = warp + 8 * u;
@@ -277,7 +306,40 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
         }
         __syncthreads();
         if (s_fail) break;
-        // split and store in the UMMA layout: offset (g * kKC + K-chunk) * 128 + r * 16
+        // split and store in the UMMA layout: offset (g * kKC + K-chunk) * 128 + row * 16
+        if constexpr (std::is_same<FT, float>::value) {
+            // four values per 16-byte load: 8-byte halves of core-matrix rows (two lanes share
+            // each bank pair: conflict-free)
+            const int rr = lane >> 2, c4 = 4 * (lane & 3);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int v = warp + 8 * u;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = 16 * h + c4;
+                    if (col < w) {
+                        float y[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            y[e] = x[u][4 * h + e] * a.scale;
+                            range_bad |= !(fabsf(y[e]) <= 65504.f);
+                        }
+                        const __half2 h0 = __floats2half2_rn(y[0], y[1]);
+                        const __half2 h1 = __floats2half2_rn(y[2], y[3]);
+                        const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+                        const __half2 l0 = __floats2half2_rn(y[0] - f0.x, y[1] - f0.y);
+                        const __half2 l1 = __floats2half2_rn(y[2] - f1.x, y[3] - f1.y);
+                        const int off = ((v & 15) * kKC + (col >> 3)) * 128 + rr * 16 + ((col & 7) >> 2) * 8;
+                        *reinterpret_cast<uint2*>(sAb + off) =
+                            make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                       *reinterpret_cast<const uint32_t*>(&h1));
+                        *reinterpret_cast<uint2*>(sAb + kAHalfBytes + off) =
+                            make_uint2(*reinterpret_cast<const uint32_t*>(&l0),
+                                       *reinterpret_cast<const uint32_t*>(&l1));
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int v = warp + 8 * u;
@@ -295,6 +357,7 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
                 *reinterpret_cast<uint4*>(sAb + off) = hi;
                 *reinterpret_cast<uint4*>(sAb + kAHalfBytes + off) = lo;
             }
+        }
         }
         // the next item's loads
         load_item(frame, it + 1, n_items, chunks, a.Ny, a.Nx, warp, r, q, x);
