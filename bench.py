@@ -458,6 +458,12 @@ def main(argv=None) -> int:
             e2e_step()
         ms_e2e = timed(e2e_step, max(2, args.steps // 2))
 
+        # the host link these frames cross: a plain pinned-to-device copy of the same bytes
+        d_copy = torch.empty_like(d_frames)
+        d_copy.copy_(h_frames, non_blocking=True)
+        ms_link = timed(lambda: d_copy.copy_(h_frames, non_blocking=True), 2)
+        del d_copy
+
         # ---- frame-to-snapshot latency (snapshot every 1024 frames) ------------------------
         lat = []
         opt.reset(stream=stream)
@@ -498,10 +504,16 @@ def main(argv=None) -> int:
         flops = 4.0 * S * K * n_per
         ach = flops / (ms_launch * 1e-3) / 1e12
         if path == "split":
+            tr_a = _traffic("accumulate_tc_kernel")
             roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
-                    "frac": ach / peaks["bf16"], "traffic": None,
-                    "note": f"algorithmic 4*S*K flops per frame; executed = 4x (split); peak "
-                            f"= {peaks['src']} bf16 dense (fp16 same rate)"}
+                    "frac": ach / peaks["bf16"],
+                    "traffic": (tr_a["bytes_per_launch"] * ACCUM_DEPTH / tr_a["frames_per_launch"])
+                               if tr_a else None,
+                    "achieved_executed": 4 * ach, "frac_executed": 4 * ach / peaks["bf16"],
+                    "note": f"one flush of {ACCUM_DEPTH} frames (split pre-pass + "
+                            f"{per_flush - 1} launches); algorithmic 4*S*K flops per frame; the "
+                            f"split path executes 4x that (hi/lo of both operands); peak = "
+                            f"{peaks['src']} bf16 dense (fp16 same rate)"}
         else:
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
@@ -609,6 +621,13 @@ def main(argv=None) -> int:
             "e2e": {"value": job_throughput(S, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": int(S * frames_bytes + 4 * S),
                     "d2h_bytes_per_step": int(4 * S),
+                    "roofline": {"bound": "host link",
+                                 "achieved": S * frames_bytes / (ms_e2e * 1e-3) / 1e9,
+                                 "peak": S * frames_bytes / (ms_link * 1e-3) / 1e9,
+                                 "unit": "GB/s",
+                                 "frac": ms_link / ms_e2e,
+                                 "note": "peak = a plain copy of the step's frames from pinned "
+                                         "host memory to the device, measured in this run"},
                     "note": "frames read by the kernels from pinned host memory; phase copied back"},
             "gpu_launches": int(launches_per_step * args.steps),
             "clocks": clk,
