@@ -247,7 +247,8 @@ wdd_status wdd_get_stage_times(wdd_plan* plan, double* ms_out, int64_t* launches
  * device wait (tensor-core pipeline barriers wait at most ~2 s).  Returns WDD_ERR_TIMEOUT and
  * clears the flag if one did; the CUDA context stays usable and the accumulator must be
  * considered invalid (wdd_reset).  Returns WDD_ERR_UNSUPPORTED (and clears the flag) when the
- * tensor-core projection met a float32 frame value outside |I| <= 65504, the range of its FP16
+ * tensor-core projection met a float32 frame value at or above the FP16 overflow threshold
+ * (|I| >= 65520) or a non-finite one, outside the range of its FP16
  * hi/lo split; the coefficients of that frame are then invalid. */
 wdd_status wdd_check_device(wdd_plan* plan);
 

@@ -894,7 +894,7 @@ wdd_status wdd_check_device(wdd_plan* P) {
     if (code == 9u) {
         WDD_CUDA(cudaMemset(P->d_status, 0, 4));
         return fail(WDD_ERR_UNSUPPORTED,
-                    "a float32 frame value is outside the FP16 split range |I| <= 65504 of the "
+                    "a float32 frame value is outside the FP16 split range |I| < 65520 of the "
                     "tensor-core projection (use the FP32 precision path for such frames)");
     }
     if (code != 0) {

@@ -6,8 +6,9 @@
 // Precision: the frame and the basis are both split into FP16 hi and lo parts,
 //   I s = I_hi + I_lo,   Bx = Bx_hi + Bx_lo,
 // with s = 1/2 for uint16 counts (so that every value up to 65535 has a finite FP16 hi part and an
-// exact lo part) and s = 1 for float32 frames, which must satisfy |I| <= 65504; a frame value
-// outside that range is reported through the plan's device status word (code 9).  The B operand
+// exact lo part) and s = 1 for float32 frames, whose values must stay below the FP16 overflow
+// threshold (|I| < 65520) and be finite; a value whose hi part overflows to infinity, or a NaN,
+// is reported through the plan's device status word (code 9).  The B operand
 // holds Bx_hi in rows 0..Lx-1 and Bx_lo in rows Lx..2Lx-1, so two MMAs per 16 columns (A = I_hi,
 // then A = I_lo) accumulate all four products; the epilogue adds the hi and lo column groups and
 // divides s out.  The representation error of each split is about 2^-22 relative, below FP32
@@ -287,7 +288,8 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
     const uint32_t idesc = idesc_f16(kTM, a.Np);
     const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
     const uint32_t sboB = (uint32_t)(a.Nx / 8) * 128u;
-    bool range_bad = false, basis_ready = false;
+    uint32_t range_bad = 0;   // float32 frames: nonzero once a hi part is infinite or NaN
+    bool basis_ready = false;
     int issued = 0, done = 0;   // items whose MMAs were issued / are known complete
 
     for (int it = 0; it < n_items; ++it) {
@@ -318,21 +320,18 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
                 for (int h = 0; h < 2; ++h) {
                     const int col = 16 * h + c4;
                     if (col < w) {
-                        float y[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            y[e] = x[u][4 * h + e] * a.scale;
-                            range_bad |= !(fabsf(y[e]) <= 65504.f);
-                        }
+                        const float* y = x[u] + 4 * h;   // scale 1 for float32 frames
                         const __half2 h0 = __floats2half2_rn(y[0], y[1]);
                         const __half2 h1 = __floats2half2_rn(y[2], y[3]);
+                        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&h0);
+                        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&h1);
+                        range_bad |= __vcmpeq2(b0 & 0x7C007C00u, 0x7C007C00u) |
+                                     __vcmpeq2(b1 & 0x7C007C00u, 0x7C007C00u);
                         const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
                         const __half2 l0 = __floats2half2_rn(y[0] - f0.x, y[1] - f0.y);
                         const __half2 l1 = __floats2half2_rn(y[2] - f1.x, y[3] - f1.y);
                         const int off = ((v & 15) * kKC + (col >> 3)) * 128 + rr * 16 + ((col & 7) >> 2) * 8;
-                        *reinterpret_cast<uint2*>(sAb + off) =
-                            make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
-                                       *reinterpret_cast<const uint32_t*>(&h1));
+                        *reinterpret_cast<uint2*>(sAb + off) = make_uint2(b0, b1);
                         *reinterpret_cast<uint2*>(sAb + kAHalfBytes + off) =
                             make_uint2(*reinterpret_cast<const uint32_t*>(&l0),
                                        *reinterpret_cast<const uint32_t*>(&l1));
@@ -345,12 +344,9 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
             const int v = warp + 8 * u;
             const int kcl = 4 * (v >> 4) + q;     // K-chunk within the chunk
             if (8 * kcl < w) {
-                float y[8];
+                float y[8];   // uint16 counts times 1/2: always within the FP16 range
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    y[e] = x[u][e] * a.scale;
-                    range_bad |= !(fabsf(y[e]) <= 65504.f);
-                }
+                for (int e = 0; e < 8; ++e) y[e] = x[u][e] * a.scale;
                 uint4 hi, lo;
                 split8(y, hi, lo);
                 const int off = ((v & 15) * kKC + kcl) * 128 + r * 16;
@@ -438,7 +434,7 @@ project_tc_kernel(const PtcArgs a, const FrameSegs segs, const IndexBlock ids) {
             __syncthreads();   // the A buffers are free again
         }
     }
-    if (range_bad) atomicExch(a.status, 9u);
+    if (range_bad != 0u) atomicExch(a.status, 9u);
     const bool failed = s_fail != 0;
 
     // second contraction: Z[ly][lx] = sum_i By[i][ly] T[i][lx], the rows of each selected
