@@ -186,6 +186,42 @@ def oracle_sample(acq, rc, frames, idx, n_sample: int):
     return time.perf_counter() - t0, os.cpu_count()
 
 
+_SINGLE_THREAD_ORACLE = r"""
+import sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle.wdd_oracle as W
+import synth
+acq, rc = synth.config(sys.argv[2])
+n = int(sys.argv[3])
+frames = np.concatenate([f for _, f in synth.frames(acq, 0, n, chunk=n)])
+idx = synth.raster_indices(acq)[:n]
+p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
+By, Bx, m_idx, comp, m_neg = W._bases(p)
+plan = W.OraclePlan(params=p, By=By, Bx=Bx, m_idx=m_idx, comp=comp, m_neg=m_neg,
+                    chi=np.zeros((1, 1)), W=np.zeros((1, rc["rank_k"])), mask=np.ones(1, bool),
+                    eps_eff=0.0)
+t0 = time.perf_counter()
+W.accumulate(W.coefficients(frames, plan), idx, p)
+print(time.perf_counter() - t0)
+"""
+
+
+def oracle_single_thread(n_sample: int):
+    """The oracle's per-frame work (projection, accumulation over every scan frequency) on one
+    host core: a subprocess with the BLAS and OpenMP pools pinned to one thread.  Returns
+    seconds or None."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD_ORACLE, root, WORKLOAD,
+                            str(n_sample)], env=env, capture_output=True, text=True, timeout=300)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def run_reference(args):
     import synth
     rank = _env_int("RANK", 0)
@@ -570,6 +606,13 @@ def main(argv=None) -> int:
         cpu = {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n_sample} frames of the workload (coefficients, accumulation over all "
                          f"{S} scan frequencies, deconvolution, inverse DFT); plan build excluded"}
+        n1 = 256
+        dt1 = oracle_single_thread(n1)
+        if dt1:
+            cpu["single_thread"] = {
+                "value": n1 / dt1, "unit": UNIT, "cores": 1,
+                "sample": f"{n1} frames: coefficients and accumulation over all {S} scan "
+                          "frequencies (the per-frame work), BLAS pinned to one thread"}
 
     if rank == 0:
         lat_ms = np.array(lat) * 1e3
