@@ -113,3 +113,49 @@ def test_plan_footprint_without_gpu(wdd):
                           det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=63)
     with pytest.raises(wdd.WddError):
         wdd.plan_footprint(bad)
+
+
+def test_classical_plan_footprint_and_validation_without_gpu(wdd):
+    """The classical plan holds the scan spectrum and the Wiener kernel, S x N^2 complex64 each;
+    its footprint and its parameter checks need no GPU."""
+    kw = dict(scan_step_m=1e-10, det_px_inv_m=1e9, voltage_v=3e5, semiconv_rad=0.02, rank_k=1)
+    p = wdd.make_params(scan_y=128, scan_x=128, det_y=128, det_x=128, **kw)
+    b = wdd.offline_footprint(p)
+    big = 2 * 128 * 128 * 128 * 128 * 8
+    assert big <= b < big + (1 << 22)
+    # against the live plan of the same geometry (the memory contrast of the comparison)
+    live = wdd.plan_footprint(wdd.make_params(scan_y=128, scan_x=128, det_y=128, det_x=128,
+                                              **dict(kw, rank_k=64)))
+    assert live * 50 < b
+    # a detector centre off pixel N/2 cannot be moved to pixel 0 by an integer roll
+    off = wdd.make_params(scan_y=8, scan_x=8, det_y=32, det_x=32, det_center_y=15.5, **kw)
+    with pytest.raises(wdd.WddError) as ei:
+        wdd.offline_footprint(off)
+    assert ei.value.status == wdd.ERR_UNSUPPORTED
+    at_half = wdd.make_params(scan_y=8, scan_x=8, det_y=32, det_x=32, det_center_y=16.0,
+                              det_center_x=16.0, **kw)
+    assert wdd.offline_footprint(at_half) > 0
+    for bad in (dict(epsilon=-1.0), dict(scan_rotation_rad=float("nan")),
+                dict(frame_dtype=7)):
+        q = wdd.make_params(scan_y=8, scan_x=8, det_y=32, det_x=32, **dict(kw, **bad))
+        with pytest.raises(wdd.WddError) as ei:
+            wdd.offline_footprint(q)
+        assert ei.value.status == wdd.ERR_INVALID_ARG
+    L = wdd.lib()
+    h = ctypes.c_void_p()
+    assert L.wdd_offline_plan_create(None, ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+    assert L.wdd_offline_reconstruct(None, None, None, None) == wdd.ERR_INVALID_ARG
+    assert L.wdd_offline_plan_destroy(None) == wdd.ERR_INVALID_ARG
+
+
+def test_rotation_and_centre_validation_without_gpu(wdd):
+    kw = dict(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=32, det_x=32, det_px_inv_m=1e9,
+              voltage_v=3e5, semiconv_rad=0.02, rank_k=16)
+    assert wdd.plan_footprint(wdd.make_params(scan_rotation_rad=1.2, **kw)) > 0
+    with pytest.raises(wdd.WddError) as ei:
+        wdd.plan_footprint(wdd.make_params(scan_rotation_rad=float("inf"), **kw))
+    assert ei.value.status == wdd.ERR_INVALID_ARG
+    L = wdd.lib()
+    cy, cx = ctypes.c_double(), ctypes.c_double()
+    assert L.wdd_detector_center(None, 1, 8, 8, 1, ctypes.byref(cy), ctypes.byref(cx),
+                                 None) == wdd.ERR_INVALID_ARG
