@@ -94,7 +94,7 @@ def sampled_rows(name, acq, basis, k, batch, n_rows=64, seed=7):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", default="c1,c2,c3crop,c3rows,c5crop,paper")
+    ap.add_argument("--only", default="c1,c2,c3crop,c3rows,c5crop,paper,c4crops")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     want = set(a.only.split(","))
@@ -119,6 +119,12 @@ def main(argv=None):
     if "paper" in want:
         acq, rc = synth.config("paper")
         rows += compare("paper-shaped", acq, rc["basis"], rc["rank_k"], rc["batch"])
+    if "c4crops" in want:
+        for i, (acq, rc) in enumerate(synth.serving_mix()):
+            crop = acq.crop(min(64, acq.scan_y), min(64, acq.scan_x))
+            rows += compare(f"c4 session {i} ({acq.scan_y}x{acq.scan_x} / {acq.det}^2, "
+                            f"{crop.scan_y}x{crop.scan_x} crop)", crop, rc["basis"], rc["rank_k"],
+                            256)
     for r in rows:
         print(json.dumps(r), flush=True)
     if a.out:

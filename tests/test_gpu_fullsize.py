@@ -7,7 +7,9 @@ and the phase against the oracle's full FP64 reconstruction of the same frames (
 held to the FP32 path's phase bound, 1e-5, and 3e-5 on the accumulator).  The same step through
 the row-factorised variant and the plain FP32 path.  At 256x256 scan / 128x128 uint16 detector,
 K = 128 (65,536 frames) the oracle checks 64 sampled accumulator rows, each computed over every
-frame.
+frame.  The 512x512-scan / 256x256-detector uint16 acquisition (K = 256) streams its first 8,192
+frames from pinned host memory in 512-frame pushes through the full-size plan; the oracle checks
+64 sampled accumulator rows over those frames.
 """
 import numpy as np
 import pytest
@@ -137,4 +139,40 @@ def test_c3_sampled_rows(torch_cuda):
         torch.cuda.synchronize()
         g.check_device()
         H = g.copy_array("accum")
+    assert rel_l2(H[rows], H_ref) < ACCUM_TOL
+
+
+def test_c5_geometry_streamed_from_pinned_host(torch_cuda):
+    """Full c5 geometry (S = 262,144 scan frequencies, 256x256 detector, K = 256, two coefficient
+    tiles per CTA), frames pushed from pinned host memory in 512-frame batches: the first 8,192
+    frames of the raster scan (a partial scan, as during an acquisition)."""
+    torch = torch_cuda
+    from paper_2212_01309_gb300 import wdd
+    from synth.torch_gen import TorchFrames
+    acq, rc = synth.config("c5")
+    n = 8192
+    B = rc["batch"]
+    gen = TorchFrames(acq)
+    h = torch.empty((n, acq.det, acq.det), dtype=torch.uint16).pin_memory()
+    for b in range(n // 256):
+        h[b * 256:(b + 1) * 256].copy_(gen.block(b).cpu())
+    frames = h.numpy()
+    idx = synth.raster_indices(acq)[:n]
+    p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=1e-3)
+    C = _coefficients(frames, _bases_plan(p, rc["rank_k"]), n)
+    rows = np.sort(np.random.default_rng(11).choice(acq.n_frames, size=64, replace=False))
+    H_ref = W.accumulate(C, idx, p, v_rows=rows)
+    prm = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                      precision="split", max_batch=B, accum_depth=4096,
+                                      coalesce_frames=1024, overlap_pushes=True)
+    stream = torch.cuda.Stream()
+    with wdd.Plan(prm) as g, torch.cuda.stream(stream):
+        for a in range(0, n, B):
+            g.push(h[a:a + B], idx[a:a + B], stream=stream)
+        _, ph, seen, covered = g.finalize(stream=stream)
+        torch.cuda.synchronize()
+        g.check_device()
+        H = g.copy_array("accum")
+    assert seen == n and covered == n
+    assert np.isfinite(ph.cpu().numpy()).all()
     assert rel_l2(H[rows], H_ref) < ACCUM_TOL
