@@ -226,6 +226,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // The next launch may start now (it holds tensor memory only where this grid does not): a
+    // following segment runs its main loop, and a following projection its loads and MMAs,
+    // on SMs this grid leaves free; both wait (griddepcontrol.wait) before touching anything
+    // this grid writes.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp < 8) {
         // ---------------- E producers: phase factors as the B operand (N rows = Re, Im) ----
@@ -399,6 +404,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         }
     }
 
+    // H (and the column maxima) may still be written by the previous launch: wait for it to
+    // complete before the epilogue reads them.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // ---------------- epilogue: warps 0-7 ----------------
     // TMEM lane = coefficient row (0-63: hi part, 64-127: lo part); column = Re v | Im v.
     // Warps whose lane quarter holds hi rows write tile T_hi[v][k], the others T_lo[v][k]
@@ -661,13 +669,26 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
         b.csplit = a.csplit + (size_t)s0 * c_stage_halves;
         b.idx = idx + (size_t)s0 * kChunk;
         b.last = s0 + seg >= stages_all ? 1 : 0;
+        // segments after the first overlap the previous one's tail (programmatic dependent
+        // launch; they read H only after griddepcontrol.wait); the first follows the split
+        // pre-pass, whose output it reads from the start
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kThreadsTC, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = s0 > 0 ? 1 : 0;
+        cudaError_t e;
         if (b.tab_mode == 2)
-            accumulate_tc_kernel<2><<<grid, kThreadsTC, smem, st>>>(b);
+            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<2>, b);
         else if (b.tab_mode == 1)
-            accumulate_tc_kernel<1><<<grid, kThreadsTC, smem, st>>>(b);
+            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<1>, b);
         else
-            accumulate_tc_kernel<0><<<grid, kThreadsTC, smem, st>>>(b);
-        cudaError_t e = cudaGetLastError();
+            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<0>, b);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
