@@ -204,10 +204,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
-        int k = k0 + t;
-        s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
-    }
     if (kTab == 1)
         for (int t = threadIdx.x; t < 2 * a.lcm; t += blockDim.x)
             s_tab[t] = a.tw16[t < a.lcm ? t : t - a.lcm];
@@ -345,6 +341,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     } else if (warp == 8) {
         // ---------------- C loader (TMA), running up to SC stages ahead ----------------
         if (lane == 0) {
+            // the split coefficients come from the launch before (the split pre-pass)
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
                                  (size_t)blockIdx.y * a.ktile_stages * cStageBytes;
             for (int it = 0; it < a.stages_total; ++it) {
@@ -421,6 +419,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         }
         const bool go = __shfl_sync(0xffffffffu, ok, 0) != 0;   // tcgen05.ld needs the whole warp
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // column scales (from the split pre-pass; read after the wait above, ordered before
+        // their use by the epilogue barrier below)
+        for (int t = threadIdx.x; t < NT; t += kProducers) {
+            const int k = k0 + t;
+            s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+        }
         const int quarter = warp & 3;                 // TMEM lanes 32 q .. 32 q + 31
         const int half = warp >> 2;                   // which half of the v columns
         const int krow = (quarter & 1) * 32 + lane;   // coefficient within the m-tile
@@ -510,6 +514,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
                                    int n, int n_pad, int K, int Kp, int NT) {
+    // the accumulation launched next sets up and generates phase factors meanwhile; it reads
+    // this kernel's output only after griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = t % Kp;
     const int b = t / Kp;
@@ -669,9 +676,10 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
         b.csplit = a.csplit + (size_t)s0 * c_stage_halves;
         b.idx = idx + (size_t)s0 * kChunk;
         b.last = s0 + seg >= stages_all ? 1 : 0;
-        // segments after the first overlap the previous one's tail (programmatic dependent
-        // launch; they read H only after griddepcontrol.wait); the first follows the split
-        // pre-pass, whose output it reads from the start
+        // every segment overlaps the launch before it (programmatic dependent launch): the first
+        // sets up and generates phase factors while the split pre-pass runs and loads the split
+        // coefficients after griddepcontrol.wait; later ones overlap the previous segment's
+        // tail and read H only after griddepcontrol.wait
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
         cfg.blockDim = dim3(kThreadsTC, 1, 1);
@@ -681,7 +689,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = s0 > 0 ? 1 : 0;
+        cfg.numAttrs = 1;
         cudaError_t e;
         if (b.tab_mode == 2)
             e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<2>, b);
