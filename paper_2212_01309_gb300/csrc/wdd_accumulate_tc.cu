@@ -515,7 +515,10 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
                                    int n, int n_pad, int K, int Kp, int NT) {
     // the accumulation launched next sets up and generates phase factors meanwhile; it reads
-    // this kernel's output only after griddepcontrol.wait
+    // this kernel's output only after griddepcontrol.wait.  Its producers read the staged scan
+    // indices at once: that is safe because this kernel is launched without programmatic
+    // serialization, so the projection that wrote them has completed before it started.  (A
+    // programmatic launch of this kernel would have to wait before releasing its dependents.)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = t % Kp;
