@@ -650,6 +650,126 @@ det_fused4_kernel(float2* G, const float2* __restrict__ K, const uint8_t* __rest
     }
 }
 
+// Two-pass detector transform for planes too large for one CTA, four-step version (power-of-
+// two sides of 256 .. 1024).  Pass 1: the ifftshift along x and the inverse transform of RB rows
+// of one scan frequency, in place; shared rows padded as in det_fused4_kernel.
+template <int N1, int N2>
+__global__ void __launch_bounds__(kOffThreads)
+det_rows4_kernel(float2* G, const float2* __restrict__ tw_g, int Ny, int RB) {
+    constexpr int N = N1 * N2;   // Nx
+    constexpr int RS = N + N / 16 + 1;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;        // N
+    float2* A = sm + N;     // RB * RS
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = tw_g[t];
+    __syncthreads();
+    const int y0 = blockIdx.y * RB;
+    const int nr = min(RB, Ny - y0);
+    float2* g = G + (size_t)blockIdx.x * Ny * N + (size_t)y0 * N;
+    auto pos = [](int r, int e) { return r * RS + e + (e >> 4); };
+    constexpr int H = N / 2;
+    for (int task = threadIdx.x; task < nr * N2; task += blockDim.x) {
+        const int j2 = task % N2, r = task / N2;
+        float2 x[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) x[j1] = g[(size_t)r * N + (((j1 * N2 + j2) + H) & (N - 1))];
+        dft_reg<N1, true>(x, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 w = tw[j2 * k1];
+            w.y = -w.y;
+            A[pos(r, k1 * N2 + j2)] = (k1 == 0 || j2 == 0) ? x[k1] : cmulf(x[k1], w);
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nr * N1; task += blockDim.x) {
+        const int k1 = task % N1, r = task / N1;
+        float2 y[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) y[j2] = A[pos(r, k1 * N2 + j2)];
+        dft_reg<N2, true>(y, tw, N1);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) g[(size_t)r * N + k1 + N1 * k2] = y[k2];
+    }
+}
+
+// Pass 2: the ifftshift along y and the inverse transform of P columns of one scan frequency;
+// MODE 0 multiplies by K and writes the block's partial sum part[v][blockIdx.y] (inactive v:
+// 0), MODE 1 writes scale * G' back and folds max |.|^2 (as det_cols_kernel).
+template <int MODE, int N1, int N2>
+__global__ void __launch_bounds__(kOffThreads)
+det_cols4_kernel(float2* G, const float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                 float2* __restrict__ part, unsigned* __restrict__ maxbits,
+                 const float2* __restrict__ tw_g, int Nx, int P, float scale) {
+    constexpr int N = N1 * N2;   // Ny
+    extern __shared__ float2 sm[];
+    __shared__ float2 red2[kOffThreads / 32];
+    __shared__ float redf[kOffThreads / 32];
+    const int v = blockIdx.x;
+    const int ncb = gridDim.y;
+    if (MODE == 0 && !mask[v]) {
+        if (threadIdx.x == 0) part[(size_t)v * ncb + blockIdx.y] = make_float2(0.f, 0.f);
+        return;
+    }
+    float2* tw = sm;        // N
+    float2* buf = sm + N;   // [k1][j2][P]
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = tw_g[t];
+    __syncthreads();
+    const int c0 = blockIdx.y * P;
+    const int np = min(P, Nx - c0);
+    const size_t npix = (size_t)N * Nx;
+    float2* g = G + (size_t)v * npix;
+    constexpr int H = N / 2;
+    for (int task = threadIdx.x; task < N2 * P; task += blockDim.x) {
+        const int j2 = task / P, p = task - (task / P) * P;
+        float2 x[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1)
+            x[j1] = p < np ? g[(size_t)(((j1 * N2 + j2) + H) & (N - 1)) * Nx + c0 + p]
+                           : make_float2(0.f, 0.f);
+        dft_reg<N1, true>(x, tw, N2);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 w = tw[j2 * k1];
+            w.y = -w.y;
+            buf[(k1 * N2 + j2) * P + p] = (k1 == 0 || j2 == 0) ? x[k1] : cmulf(x[k1], w);
+        }
+    }
+    __syncthreads();
+    float2 acc = make_float2(0.f, 0.f);
+    float mx = 0.f;
+    const float2* kv = K + (size_t)v * npix;
+    for (int task = threadIdx.x; task < N1 * P; task += blockDim.x) {
+        const int k1 = task / P, p = task - (task / P) * P;
+        float2 y[N2];
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) y[j2] = buf[(k1 * N2 + j2) * P + p];
+        dft_reg<N2, true>(y, tw, N1);
+        if (p >= np) continue;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const size_t e = (size_t)(k1 + N1 * k2) * Nx + c0 + p;
+            const float2 val = y[k2];
+            if (MODE == 0) {
+                const float2 k = kv[e];
+                acc.x = fmaf(val.x, k.x, fmaf(-val.y, k.y, acc.x));
+                acc.y = fmaf(val.x, k.y, fmaf(val.y, k.x, acc.y));
+            } else {
+                const float2 w = make_float2(val.x * scale, val.y * scale);
+                g[e] = w;
+                mx = fmaxf(mx, w.x * w.x + w.y * w.y);
+            }
+        }
+    }
+    if (MODE == 0) {
+        const float2 sres = block_sum2(acc, red2);
+        if (threadIdx.x == 0) part[(size_t)v * ncb + blockIdx.y] = sres;
+    } else {
+        const float m = block_max(mx, redf);
+        if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
+    }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 
 int scan_pixels_per_cta(int n) {
@@ -684,6 +804,7 @@ int cols_per_cta(int Ny) {
 #define WDD_FOUR_STEP_SIZES(X) X(32, 8, 4) X(64, 8, 8) X(128, 16, 8) X(256, 16, 16) \
     X(512, 32, 16) X(1024, 32, 32)
 #define WDD_DET4_SIZES(X) X(32, 8, 4) X(64, 8, 8) X(128, 16, 8)
+#define WDD_DET2P4_SIZES(X) X(256, 16, 16) X(512, 32, 16) X(1024, 32, 32)
 
 bool four_step_len(int n) {
 #define WDD_FS_CASE(nn, a, b) if (n == nn) return true;
@@ -692,6 +813,7 @@ bool four_step_len(int n) {
     return false;
 }
 bool det4_square(int Ny, int Nx) { return Ny == Nx && (Nx == 32 || Nx == 64 || Nx == 128); }
+bool det2p4_len(int n) { return n == 256 || n == 512 || n == 1024; }
 int scan4_pixels_per_cta(int n) { return std::min(64, std::max(8, kScanLineElems / n)); }
 size_t scan4_smem(int n) {
     return sizeof(float2) * ((size_t)n + (size_t)n * scan4_pixels_per_cta(n));
@@ -715,6 +837,12 @@ cudaError_t for_each_offline_kernel(F f) {
     WDD_OFF_K((det_fused4_kernel<1, a, b>));
     WDD_DET4_SIZES(WDD_OFF_D4)
 #undef WDD_OFF_D4
+#define WDD_OFF_2P4(nn, a, b)                                  \
+    WDD_OFF_K((det_rows4_kernel<a, b>));                       \
+    WDD_OFF_K((det_cols4_kernel<0, a, b>));                    \
+    WDD_OFF_K((det_cols4_kernel<1, a, b>));
+    WDD_DET2P4_SIZES(WDD_OFF_2P4)
+#undef WDD_OFF_2P4
     WDD_OFF_K((scan_axis_kernel<uint16_t, true>));
     WDD_OFF_K((scan_axis_kernel<uint16_t, false>));
     WDD_OFF_K((scan_axis_kernel<float, true>));
@@ -797,6 +925,30 @@ cudaError_t launch_detector(const wdd_offline_plan* P, float2* X, cudaStream_t s
         else
             det_fused_kernel<MODE, false><<<P->S, kDetThreads, smem, st>>>(
                 X, P->d_K, P->d_mask, P->d_o, P->d_max, P->d_tw_dy, P->d_tw_dx, Ny, Nx, ly, lx, scale);
+        return cudaGetLastError();
+    }
+    if (det2p4_len(Nx) && det2p4_len(Ny)) {
+        {
+            dim3 grid(P->S, (Ny + P->rb - 1) / P->rb);
+            const size_t smem = sizeof(float2) * ((size_t)Nx + (size_t)P->rb * (Nx + Nx / 16 + 1));
+#define WDD_ROWS4(nn, a, b)                                                                    \
+            if (Nx == nn) det_rows4_kernel<a, b><<<grid, kOffThreads, smem, st>>>(X, P->d_tw_dx, Ny, P->rb);
+            WDD_DET2P4_SIZES(WDD_ROWS4)
+#undef WDD_ROWS4
+        }
+        {
+            dim3 grid(P->S, P->ncb);
+            const size_t smem = sizeof(float2) * ((size_t)Ny + (size_t)Ny * P->cp);
+#define WDD_COLS4(nn, a, b)                                                                    \
+            if (Ny == nn)                                                                      \
+                det_cols4_kernel<MODE, a, b><<<grid, kOffThreads, smem, st>>>(                 \
+                    X, P->d_K, P->d_mask, P->d_part, P->d_max, P->d_tw_dy, Nx, P->cp, scale);
+            WDD_DET2P4_SIZES(WDD_COLS4)
+#undef WDD_COLS4
+        }
+        if (MODE == 0)
+            det_reduce_kernel<<<(P->S + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
+                P->d_part, P->d_mask, P->d_o, P->S, P->ncb, scale);
         return cudaGetLastError();
     }
     {

@@ -2,8 +2,8 @@
 
 The GPU path runs the 4-D transform in FP32 (twiddles and Y_v built in FP64), so it is held to
 the FP32 path's bounds: spectrum and phase relative L2 <= 1e-5, the Wiener kernel to 1e-5.
-Cases cover power-of-two and other scan and detector sizes (radix-2 and direct-DFT transforms),
-detector planes that fit one CTA and ones that take the two-pass transform, every frame type,
+Cases cover power-of-two and other scan and detector sizes (four-step, radix-2 and direct-DFT
+transforms), detector planes that fit one CTA and ones that take the two-pass transform, every frame type,
 device and pinned sources, a scan rotation, the absolute-epsilon mode, the live = classical
 identity of the full Fourier basis on the GPU, and a 128^2 scan / 128^2 detector dataset checked
 on sampled frequencies.
@@ -62,7 +62,8 @@ CASES = [
     ((16, 16), 32, "f32", 1),
     ((12, 18), 24, "u16", 1),       # direct DFT on both scan axes and the detector
     ((20, 14), 40, "f64", 1),
-    ((8, 8), 256, "u16", 0),        # two-pass detector transform (radix-2)
+    ((8, 8), 256, "u16", 0),        # two-pass detector transform (four-step, 16 x 16)
+    ((4, 4), 512, "f32", 0),        # two-pass detector transform (four-step, 32 x 16)
     ((6, 7), 120, "f32", 0),        # two-pass detector transform (direct DFT)
     ((32, 32), 128, "u16", 1),      # the 128-pixel detector of the bench
 ]
