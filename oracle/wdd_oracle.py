@@ -24,7 +24,7 @@ Readings of the paper (each one is also listed in the design notes):
   R5 epsilon is relative: eps_eff = epsilon * max_{v,m} |chi_v[m]|^2 (an absolute mode exists).
   R6 Eq. 3's division by sqrt(o_0) is applied (principal root; skipped when o_0 == 0), then the
      conjugated inverse DFT of Algorithm 2 with numpy's 1/S normalisation.
-  R7 Sum of all elements of D_v is the zero-frequency extraction, used literally.
+  R7 The sum over every element of D_v is the zero-frequency extraction, used as written.
   R8 A frequency is active iff the two aperture discs overlap: |q_v| < 2 theta / lambda (strict).
   R9 Sign conventions: P_s = p(r - r_s); scan kernel exp(-2 pi i q_v . r_s); Y_v(q) =
      p(q) conj p(q + q_v); probe p(k) = [|k| <= theta/lambda] exp(-i pi lambda df |k|^2).
@@ -419,7 +419,7 @@ def accumulate(C: np.ndarray, scan_idx: np.ndarray, p: Params,
 
 
 def deconvolve(H: np.ndarray, plan: OraclePlan, v_rows: np.ndarray | None = None) -> np.ndarray:
-    """Algorithm 2: D_v = t_v o K_v, o_v = sum of all elements of D_v (reading R2, R7)."""
+    """Algorithm 2: D_v = t_v o K_v, o_v = the sum over every element of D_v (reading R2, R7)."""
     W = plan.W if v_rows is None else plan.W[v_rows]
     return (W * H).sum(axis=1)
 

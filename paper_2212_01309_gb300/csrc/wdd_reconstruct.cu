@@ -1,5 +1,5 @@
 // Snapshot reconstruction (Algorithm 2, after the frame loop; Eq. 3):
-//   o_v = sum_k W_v[k] H[v, k]                 (Hadamard product with K_v, sum of all elements)
+//   o_v = sum_k W_v[k] H[v, k]                 (Hadamard product with K_v, summed over every element)
 //   O   = conj( IDFT2( o / sqrt(o_0) ) )        (numpy ifft2 normalisation 1/S)
 //   phase = atan2(Im O, Re O)
 // The deconvolution reads H and W once (HBM bound); the inverse DFT runs
