@@ -397,3 +397,23 @@ def test_relative_epsilon_is_scale_free():
     _, a = W.finalize(W.live_wdd(F, idx, plan), p)
     _, b = W.finalize(W.live_wdd(17.0 ** 2 * F, idx, plan), p)
     assert np.allclose(a, b, atol=1e-12)
+
+
+def test_live_equals_offline_non_square_detector():
+    """A 24 x 32 detector: rows 4 .. 27 of 32 x 32 frames keep the zero frequency at
+    (det_y // 2, det_x // 2); the full Fourier basis still reproduces classical WDD exactly."""
+    acq = c1_odd(defocus_m=5e-9)
+    acq = dataclasses.replace(acq, scan_y=9, scan_x=11, obj_y=18, obj_x=22)
+    F = synth.all_frames(acq)[:, 4:28, :]
+    p = W.Params(scan_y=acq.scan_y, scan_x=acq.scan_x, scan_step_m=acq.scan_step_m, det_y=24,
+                 det_x=32, det_px_inv_m=acq.det_px_inv_m, voltage_v=acq.voltage_v,
+                 semiconv_rad=acq.semiconv_rad, defocus_m=acq.defocus_m, epsilon=1e-3,
+                 rank_k=24 * 32, basis="fourier_full")
+    idx = synth.raster_indices(acq)
+    o_live = W.live_wdd(F, idx, W.build_plan(p))
+    o_off = W.offline_wdd(F, p)
+    assert W.complex_rel_l2(o_live, o_off) < 1e-10
+    # and it is not the square result: dropping detector rows changes the spectrum
+    p_sq = dataclasses.replace(p, det_y=32, rank_k=32 * 32)
+    o_sq = W.offline_wdd(synth.all_frames(acq), p_sq)
+    assert W.complex_rel_l2(o_off, o_sq) > 1e-3
