@@ -101,3 +101,20 @@ def test_center_of_mass_of_simulated_frames():
     acq = dataclasses.replace(odd_acq(), det=32, dtype="f32", dose=None)
     cy, cx = W.detector_center_of_mass(synth.all_frames(acq))
     assert abs(cy - 16.0) < 0.25 and abs(cx - 16.0) < 0.25
+
+
+@pytest.mark.parametrize("turns", [1, 2, 3])
+def test_quarter_turns_in_classical_wdd(turns):
+    """The same identity through the classical route (Eq. 2-3): Y_v with the rotated shift, the
+    detector transforms of the turned frames."""
+    acq = odd_acq(defocus_m=5e-9)
+    F = synth.all_frames(acq)
+    p0 = W.Params.from_acquisition(acq, basis="fourier_full", rank_k=acq.det * acq.det,
+                                   epsilon=1e-3)
+    o0 = W.offline_wdd(F, p0)
+    Fr = np.ascontiguousarray(np.rot90(F, k=turns, axes=(1, 2)))
+    o1 = W.offline_wdd(Fr, dataclasses.replace(p0, scan_rotation_rad=turns * math.pi / 2))
+    assert W.complex_rel_l2(o1, o0) < 1e-9
+    # without the rotation the turned frames give another spectrum (compared without the
+    # dominant v = 0 term)
+    assert W.complex_rel_l2(W.offline_wdd(Fr, p0)[1:], o0[1:]) > 1e-2
