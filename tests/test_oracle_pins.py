@@ -417,3 +417,19 @@ def test_live_equals_offline_non_square_detector():
     p_sq = dataclasses.replace(p, det_y=32, rank_k=32 * 32)
     o_sq = W.offline_wdd(synth.all_frames(acq), p_sq)
     assert W.complex_rel_l2(o_off, o_sq) > 1e-3
+
+
+def test_classical_result_ignores_the_detector_roll(monkeypatch):
+    """A common circular shift of the data and of Y_v multiplies both inverse detector transforms
+    by the same phase ramp, which the conjugate in the Wiener kernel cancels: o_v does not depend
+    on how the zero frequency is moved to index 0 (checked on an odd detector, where moving it by
+    fftshift instead of ifftshift is a different roll)."""
+    c1, _ = synth.config("c1")
+    acq = dataclasses.replace(c1, scan_y=9, scan_x=11, obj_y=18, obj_x=22, det=15,
+                              defocus_m=4e-9, dtype="f64", dose=None)
+    F = synth.all_frames(acq)
+    p = W.Params.from_acquisition(acq, basis="fourier_full", rank_k=15 * 15, epsilon=1e-3)
+    ref = W.offline_wdd(F, p)
+    assert not np.array_equal(np.fft.fftshift(np.arange(15)), np.fft.ifftshift(np.arange(15)))
+    monkeypatch.setattr(W.np.fft, "ifftshift", lambda x, axes=None: np.fft.fftshift(x, axes=axes))
+    assert W.complex_rel_l2(W.offline_wdd(F, p), ref) < 1e-12
