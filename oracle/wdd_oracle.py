@@ -31,6 +31,20 @@ Readings of the paper (each one is also listed in the design notes):
   R15 Scan rotation (Tables 2 and 3): the scan-axis frequency (q_y, q_x) shifts the probe by
      (q_y cos t - q_x sin t, q_y sin t + q_x cos t) on the detector; t = +90 degrees equals the
      detector images turned by numpy's rot90 over their two axes.
+  R17 An object or probe estimate lives on the scan grid; its spectrum at any detector-pixel
+     frequency is the trigonometric sum over the scan positions (periodic in the scan's
+     reciprocal lattice), which equals fft2 at the scan frequencies.
+  R18 The object's counterpart of Y_v is Omega_v(q) = Psi(q) conj Psi(q - q_v): the scan
+     transform of noiseless data is the convolution over q of Y_v and Omega_v.
+  R19 Probe reconstruction (Sect. 10) runs Algorithm 1-2 (or Eq. 2) with Y_v replaced by
+     Omega_v; the zero-frequency sum p_v then carries p(0) conj p(q_v), so the probe spectrum
+     on the scan lattice is conj(p_v / sqrt(p_0)).  The updated Wiener filter takes Y_v from the
+     recovered probe's spectrum at detector pixels (R17).
+  R20 The swapped Wiener filter takes epsilon relative to each frequency's own maximum of
+     |Omega_v| (reduced or per pixel): the object's autocorrelation at v != 0 is smaller than at
+     v = 0 by the object's contrast squared, so one maximum over all v would swamp every v != 0.
+  R21 The updated Wiener filter keeps the known condenser aperture (amplitude 1 for
+     |k| <= theta / lambda) and takes only the phase inside it from the recovered probe.
 """
 from __future__ import annotations
 
@@ -46,7 +60,9 @@ __all__ = [
     "coefficients", "phase_factor", "accumulate", "deconvolve", "finalize", "live_wdd",
     "live_wdd_per_frame", "offline_wdd", "offline_probe_wigner", "offline_wdd_frequency",
     "phase_rel_l2", "complex_rel_l2", "active_mask", "fourier_window_plan", "scan_shift_det_px",
-    "detector_center_of_mass",
+    "detector_center_of_mass", "scan_grid_spectrum_at", "object_autocorrelation",
+    "build_probe_plan", "probe_finalize", "live_probe", "offline_probe_wdd",
+    "recovered_probe_spectrum_at", "recovered_probe_autocorrelation", "updated_plan",
 ]
 
 # CODATA 2018 constants (SI).
@@ -327,7 +343,7 @@ def _bases(p: Params):
     return By, Bx, m_idx, comp, m_idx.copy()
 
 
-def build_plan(p: Params) -> OraclePlan:
+def build_plan(p: Params, autocorrelation=None, eps_per_frequency: bool = False) -> OraclePlan:
     """Algorithm 1: for every scan frequency v build Y_v, reduce it, form the Wiener filter.
 
     chi_v = H(Y_v) (complex), K_v = conj(chi_v) / (|chi_v|^2 + eps_eff), then the weights W_v[k]
@@ -335,17 +351,27 @@ def build_plan(p: Params) -> OraclePlan:
     for the Fourier family the cos/sin rows of r and -r are paired,
         W[cos r] = K(r) + K(-r)   (K(r) alone when r = -r),   W[sin r] = i (K(r) - K(-r)),
     which is the same sum over all r written with real coefficients.  Inactive v get W_v = 0.
+
+    ``autocorrelation(vy, vx)`` replaces Y_v when given: the object's autocorrelation for the
+    swapped deconvolution that recovers the probe, or the autocorrelation of a recovered probe
+    for the updated Wiener filter (Sect. 10, readings R17-R21).  With ``eps_per_frequency`` the
+    relative epsilon takes the maximum over each frequency's own coefficients (reading R20).
     """
     By, Bx, m_idx, comp, m_neg = _bases(p)
     M = By.shape[1] * Bx.shape[1]
     chi = np.zeros((p.S, M), dtype=np.complex128)
     for vy in range(p.scan_y):
         for vx in range(p.scan_x):
-            Y = probe_autocorrelation(p, vy, vx)
+            if autocorrelation is None:
+                Y = probe_autocorrelation(p, vy, vx)
+            else:
+                Y = autocorrelation(vy, vx)
             chi[vy * p.scan_x + vx] = project_operator(Y, By, Bx).reshape(-1)
     used = np.unique(np.concatenate([m_idx, m_neg]))
     if p.eps_absolute:
         eps_eff = p.epsilon
+    elif eps_per_frequency:
+        eps_eff = p.epsilon * np.max(np.abs(chi[:, used]) ** 2, axis=1, keepdims=True)
     else:
         eps_eff = p.epsilon * float(np.max(np.abs(chi[:, used]) ** 2))
     Kv = np.conj(chi) / (np.abs(chi) ** 2 + eps_eff)
@@ -428,8 +454,8 @@ def finalize(o: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
     """Eq. 3 normalisation by sqrt(o_0), then conj(F^-1(O)) of Algorithm 2 (reading R6).
 
     Returns (complex object transfer function S_y x S_x, phase in radians).  The phase is pinned
-    (weak-phase recovery, roll and conjugation invariants); the absolute amplitude scale is
-    parity unpinned.
+    (weak-phase recovery, roll and conjugation invariants), and the amplitude scale by the exact
+    recovery of an object from noiseless periodic data (unit scale, up to the phase of Psi(0)).
     """
     o = np.asarray(o, dtype=np.complex128).reshape(p.scan_y, p.scan_x)
     o0 = o[0, 0]
@@ -515,6 +541,126 @@ def offline_wdd(frames: np.ndarray, p: Params) -> np.ndarray:
     WO = GP * np.conj(WP) / (np.abs(WP) ** 2 + eps_eff)
     o = WO.sum(axis=(2, 3)).reshape(-1)
     return np.where(active_mask(p), o, 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Probe reconstruction by swapping the deconvolution (Sect. 10), readings R17-R21
+# ---------------------------------------------------------------------------------------------
+
+def scan_grid_spectrum_at(X: np.ndarray, p: Params, ky_px, kx_px) -> np.ndarray:
+    """Spectrum of an array given on the scan grid (an object or probe estimate), evaluated at
+    detector-pixel frequencies (ky, kx) along the detector axes (reading R17).
+
+    X(k) = sum_s X_s exp(-2 pi i dk k . r_s), with r_s = (s_y, s_x) * Delta the scan position
+    turned onto the detector axes by the scan rotation (R15), so that dk k . r_s is the scan-axis
+    frequency R^T k times the position.  At the detector image of a scan frequency q_v this is
+    numpy's fft2 of X at v.
+    """
+    X = np.asarray(X, dtype=np.complex128).reshape(p.scan_y, p.scan_x)
+    ky = np.asarray(ky_px, dtype=np.float64)
+    kx = np.asarray(kx_px, dtype=np.float64)
+    c, s = math.cos(p.scan_rotation_rad), math.sin(p.scan_rotation_rad)
+    a = (c * ky + s * kx) * (p.det_px_inv_m * p.scan_step_m)   # cycles per scan step, scan y
+    b = (-s * ky + c * kx) * (p.det_px_inv_m * p.scan_step_m)  # and scan x
+    Ey = np.exp(-2j * np.pi * a[..., None] * np.arange(p.scan_y))
+    Ex = np.exp(-2j * np.pi * b[..., None] * np.arange(p.scan_x))
+    return np.einsum("...y,yx,...x->...", Ey, X, Ex, optimize=True)
+
+
+def object_autocorrelation(obj: np.ndarray, p: Params, vy: int, vx: int) -> np.ndarray:
+    """The object's counterpart of Y_v on the detector grid (reading R18):
+    Omega_v(q) = Psi(q) conj Psi(q - q_v), Psi the spectrum of the object estimate
+    (scan_grid_spectrum_at), q in pixels from the detector centre.  The data's scan transform is
+    the convolution over q of Y_v with Omega_v, which is what lets the two swap roles."""
+    dy, dx = scan_shift_det_px(p, vy, vx)
+    qy = np.arange(p.det_y, dtype=np.float64) - p.cy
+    qx = np.arange(p.det_x, dtype=np.float64) - p.cx
+    ky, kx = np.meshgrid(qy, qx, indexing="ij")
+    a = scan_grid_spectrum_at(obj, p, ky, kx)
+    b = scan_grid_spectrum_at(obj, p, ky - dy, kx - dx)
+    return a * np.conj(b)
+
+
+def build_probe_plan(obj: np.ndarray, p: Params) -> OraclePlan:
+    """Algorithm 1 with the roles swapped (Sect. 10): the Wiener filter of every scan frequency
+    built from the reduced object autocorrelation instead of the probe's, with epsilon relative
+    to each frequency's own maximum (reading R20) and the overlap mask of R8."""
+    return build_plan(p, lambda vy, vx: object_autocorrelation(obj, p, vy, vx),
+                      eps_per_frequency=True)
+
+
+def probe_finalize(pv: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
+    """Probe from the swapped deconvolution (reading R19).
+
+    The zero-frequency sum of the deconvolved probe Wigner distribution at scan frequency v is
+    p(0) conj p(q_v) times a constant, so the probe spectrum at the scan-lattice frequencies is
+    conj(p_v / sqrt(p_0)) (principal root, skipped when p_0 == 0, as R6); its inverse DFT with
+    numpy's 1/S is the probe on the scan grid.  Returns (spectrum, probe), both S_y x S_x, with
+    the zero frequency and the probe's origin at index 0.
+    """
+    pv = np.asarray(pv, dtype=np.complex128).reshape(p.scan_y, p.scan_x)
+    p0 = pv[0, 0]
+    scale = 1.0 / np.sqrt(p0) if p0 != 0 else 1.0
+    spec = np.conj(pv * scale)
+    return spec, np.fft.ifft2(spec)
+
+
+def live_probe(H: np.ndarray, obj: np.ndarray, p: Params) -> tuple[np.ndarray, np.ndarray]:
+    """Probe from the live accumulator H (Eq. 14) and an object estimate: the swapped filter
+    applied to H, the sum over every coefficient (R7), then probe_finalize."""
+    return probe_finalize(deconvolve(H, build_probe_plan(obj, p)), p)
+
+
+def offline_probe_wdd(frames: np.ndarray, obj: np.ndarray, p: Params) -> np.ndarray:
+    """Classical WDD with the roles swapped (Eq. 2 with W_O and W_P exchanged, Sect. 10):
+    W_O(v, r) = F_q^-1(Omega_v), W_P = F_q^-1(G_v) conj(W_O) / (|W_O|^2 + eps_eff),
+    p_v = F_r(W_P)|_{q=0} = sum_r W_P; eps_eff(v) = epsilon * max_r |W_O(v, r)|^2 (reading R20;
+    or absolute), inactive frequencies zeroed.  Returns p (S complex) for probe_finalize."""
+    if p.cy != p.det_y // 2 or p.cx != p.det_x // 2:
+        raise ValueError("offline WDD assumes the detector centre at N//2")
+    I4 = np.asarray(frames, dtype=np.float64).reshape(p.scan_y, p.scan_x, p.det_y, p.det_x)
+    G = np.fft.fft2(I4, axes=(0, 1))
+    WO = np.empty((p.scan_y, p.scan_x, p.det_y, p.det_x), dtype=np.complex128)
+    for vy in range(p.scan_y):
+        for vx in range(p.scan_x):
+            WO[vy, vx] = np.fft.ifft2(np.fft.ifftshift(object_autocorrelation(obj, p, vy, vx)))
+    if p.eps_absolute:
+        eps_eff = p.epsilon
+    else:
+        eps_eff = p.epsilon * np.max(np.abs(WO) ** 2, axis=(2, 3), keepdims=True)
+    GP = np.fft.ifft2(np.fft.ifftshift(G, axes=(2, 3)), axes=(2, 3))
+    WP = GP * np.conj(WO) / (np.abs(WO) ** 2 + eps_eff)
+    pv = WP.sum(axis=(2, 3)).reshape(-1)
+    return np.where(active_mask(p), pv, 0.0)
+
+
+def recovered_probe_spectrum_at(probe: np.ndarray, p: Params, ky_px, kx_px) -> np.ndarray:
+    """A recovered probe as a probe model for Algorithm 1 (reading R21): the condenser aperture
+    is kept, |k| <= theta / lambda with amplitude 1, and the recovered probe supplies the phase
+    inside it (the phase of its spectrum at detector pixels, scan_grid_spectrum_at)."""
+    ky = np.asarray(ky_px, dtype=np.float64)
+    kx = np.asarray(kx_px, dtype=np.float64)
+    r = bright_field_radius_px(p)
+    amp = (ky * ky + kx * kx <= r * r).astype(np.float64)
+    return amp * np.exp(1j * np.angle(scan_grid_spectrum_at(probe, p, ky, kx)))
+
+
+def recovered_probe_autocorrelation(probe: np.ndarray, p: Params, vy: int, vx: int) -> np.ndarray:
+    """Y_v from a recovered probe (the Wiener update of Sect. 10): p(q) conj p(q + q_v) with p
+    the recovered probe model of recovered_probe_spectrum_at."""
+    dy, dx = scan_shift_det_px(p, vy, vx)
+    qy = np.arange(p.det_y, dtype=np.float64) - p.cy
+    qx = np.arange(p.det_x, dtype=np.float64) - p.cx
+    ky, kx = np.meshgrid(qy, qx, indexing="ij")
+    a = recovered_probe_spectrum_at(probe, p, ky, kx)
+    b = recovered_probe_spectrum_at(probe, p, ky + dy, kx + dx)
+    return a * np.conj(b)
+
+
+def updated_plan(probe: np.ndarray, p: Params) -> OraclePlan:
+    """Algorithm 1 rebuilt from a recovered probe: the updated Wiener filter that re-deconvolves
+    the retained accumulator H into a refined object (Sect. 10)."""
+    return build_plan(p, lambda vy, vx: recovered_probe_autocorrelation(probe, p, vy, vx))
 
 
 # ---------------------------------------------------------------------------------------------
