@@ -338,6 +338,21 @@ typedef struct wdd_offline_plan wdd_offline_plan;
 /* Builds the Wiener kernel for every scan frequency (synchronous).  Errors: INVALID_ARG,
  * UNSUPPORTED (detector centre not det / 2, sizes), OUT_OF_MEMORY (budget or allocation), CUDA. */
 wdd_status wdd_offline_plan_create(const wdd_params* p, wdd_offline_plan** out);
+/* Probe reconstruction (Sect. 10): a classical plan with the roles of probe and object swapped.
+ * The Wiener kernel is built from an object estimate `obj` (complex64 [scan_y][scan_x], e.g. the
+ * out->obj of a reconstruction; device or pinned host memory, read during this call only):
+ * Omega_v(q) = Psi(q) conj Psi(q - q_v) with Psi(k) = sum_s obj_s exp(-2 pi i dk k . r_s) the
+ * estimate's spectrum at detector-pixel frequencies, W_O = IFFT2(ifftshift Omega_v), and
+ * conj(W_O) / (|W_O|^2 + eps_v) with eps_v = epsilon * max_r |W_O(v, r)|^2 per frequency (or
+ * epsilon when eps_absolute).  wdd_offline_reconstruct on this plan then writes the probe
+ * IFFT2(conj(p_v / sqrt(p_0))) on the scan grid (origin at index 0) to out->obj and its phase
+ * to out->phase; WDD_OFFLINE_SPECTRUM holds p_v, and get_info's eps_eff the largest eps_v.
+ * Holds the classical plan's memory plus two scan-axis tables and the object's x sums.
+ * Errors: as wdd_offline_plan_create; INVALID_ARG for a NULL or pageable `obj` or an estimate
+ * whose autocorrelation is zero everywhere; UNSUPPORTED for scan_rotation_rad != 0 (the
+ * estimate's spectrum is taken one scan axis at a time). */
+wdd_status wdd_offline_probe_plan_create(const wdd_params* p, const void* obj,
+                                         wdd_offline_plan** out);
 /* Device bytes such a plan would hold, without touching the GPU. */
 wdd_status wdd_offline_footprint(const wdd_params* p, int64_t* bytes);
 /* Reconstructs from all S = scan_y * scan_x frames: frames [S][det_y][det_x] of frame_dtype in

@@ -374,7 +374,11 @@ def build_plan(p: Params, autocorrelation=None, eps_per_frequency: bool = False)
         eps_eff = p.epsilon * np.max(np.abs(chi[:, used]) ** 2, axis=1, keepdims=True)
     else:
         eps_eff = p.epsilon * float(np.max(np.abs(chi[:, used]) ** 2))
-    Kv = np.conj(chi) / (np.abs(chi) ** 2 + eps_eff)
+    if eps_per_frequency:   # a frequency whose autocorrelation vanishes carries nothing: 0
+        den = np.abs(chi) ** 2 + eps_eff
+        Kv = np.divide(np.conj(chi), den, out=np.zeros_like(chi), where=den > 0)
+    else:
+        Kv = np.conj(chi) / (np.abs(chi) ** 2 + eps_eff)
     if p.basis == "fourier_full":
         self_conj = m_idx == m_neg
         Kr = Kv[:, m_idx]
@@ -615,7 +619,8 @@ def offline_probe_wdd(frames: np.ndarray, obj: np.ndarray, p: Params) -> np.ndar
     """Classical WDD with the roles swapped (Eq. 2 with W_O and W_P exchanged, Sect. 10):
     W_O(v, r) = F_q^-1(Omega_v), W_P = F_q^-1(G_v) conj(W_O) / (|W_O|^2 + eps_eff),
     p_v = F_r(W_P)|_{q=0} = sum_r W_P; eps_eff(v) = epsilon * max_r |W_O(v, r)|^2 (reading R20;
-    or absolute), inactive frequencies zeroed.  Returns p (S complex) for probe_finalize."""
+    or absolute), inactive frequencies zeroed, and so is a frequency whose W_O vanishes
+    everywhere (nothing to divide by).  Returns p (S complex) for probe_finalize."""
     if p.cy != p.det_y // 2 or p.cx != p.det_x // 2:
         raise ValueError("offline WDD assumes the detector centre at N//2")
     I4 = np.asarray(frames, dtype=np.float64).reshape(p.scan_y, p.scan_x, p.det_y, p.det_x)
@@ -629,7 +634,9 @@ def offline_probe_wdd(frames: np.ndarray, obj: np.ndarray, p: Params) -> np.ndar
     else:
         eps_eff = p.epsilon * np.max(np.abs(WO) ** 2, axis=(2, 3), keepdims=True)
     GP = np.fft.ifft2(np.fft.ifftshift(G, axes=(2, 3)), axes=(2, 3))
-    WP = GP * np.conj(WO) / (np.abs(WO) ** 2 + eps_eff)
+    den = np.abs(WO) ** 2 + eps_eff
+    K = np.divide(np.conj(WO), den, out=np.zeros_like(WO), where=den > 0)
+    WP = GP * K
     pv = WP.sum(axis=(2, 3)).reshape(-1)
     return np.where(active_mask(p), pv, 0.0)
 

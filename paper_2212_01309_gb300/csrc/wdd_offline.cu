@@ -52,6 +52,15 @@ struct wdd_offline_plan {
     float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
     float2* d_part = nullptr;    // [S][ncb] partial sums of the two-pass detector transform
     unsigned* d_max = nullptr;   // [1] max |W_P|^2 (float bits)
+    // probe reconstruction (Sect. 10): K built from an object estimate instead of the probe
+    int swapped = 0;
+    float2* d_Ey = nullptr;      // [Sy][Ny][Sy] scan-y sums at detector row i - cy - qy[vy]
+    float2* d_Ey0 = nullptr;     // [Ny][Sy] the same without the shift
+    float2* d_Ex = nullptr;      // [Sx][Nx][Sx]
+    float2* d_Ex0 = nullptr;     // [Nx][Sx]
+    float2* d_T = nullptr;       // [Sx][Sy][Nx] x sums of the object estimate per x shift
+    float2* d_T0 = nullptr;      // [Sy][Nx]
+    float* d_vmax = nullptr;     // [S] max_r |W_O(v, r)|^2
     std::vector<wdd::DevBuf> allocs;
     int64_t device_bytes = 0;
 };
@@ -87,6 +96,10 @@ __device__ __forceinline__ int brev_bits(int j, int logn) {
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 cfmaf(float2 a, float2 b, float2 c) {  // c + a b
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 
 __device__ __forceinline__ float2 as_c(uint16_t v) { return make_float2((float)v, 0.f); }
@@ -463,6 +476,124 @@ __global__ void wiener_kernel(float2* __restrict__ K, const uint8_t* __restrict_
         const float d = w.x * w.x + w.y * w.y + eps;
         K[t] = make_float2(w.x / d, -w.y / d);
     }
+}
+
+// ---- probe reconstruction (Sect. 10): the deconvolution with the roles swapped.  The Wiener
+// kernel is built from Omega_v(q) = Psi(q) conj Psi(q - q_v), Psi the spectrum of an object
+// estimate given on the scan grid, evaluated at detector-pixel frequencies as the trigonometric
+// sum over the scan positions.  Without a scan rotation that sum separates into one sum per
+// scan axis, which is what the tables below hold.
+
+// E[(v * n + i) * ns + s] = exp(-2 pi i frac(((i - c - q[v]) * dks) * s)) for v < nv, i < n,
+// s < ns: one axis of the trigonometric sum at detector-pixel frequency i - c - q[v] (q == NULL:
+// no shift, nv = 1).  dks = dk * scan step; the phase is reduced to one turn in FP64.
+__global__ void axis_dtft_table_kernel(float2* __restrict__ E, const double* __restrict__ q, int nv,
+                                       int n, int ns, double c, double dks) {
+    const int64_t total = (int64_t)nv * n * ns;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(t % ns);
+        const int64_t r = t / ns;
+        const int i = (int)(r % n);
+        const int v = (int)(r / n);
+        const double k = (double)i - c - (q ? q[v] : 0.0);
+        const double ph = (k * dks) * (double)s;
+        const double f = ph - floor(ph);
+        double sn, cs;
+        sincospi(-2.0 * f, &sn, &cs);
+        E[t] = make_float2((float)cs, (float)sn);
+    }
+}
+
+// T[(u * Sy + sy) * Nx + j] = sum_sx O[sy][sx] Ex[(u * Nx + j) * Sx + sx] for u < nu: the sums of
+// the object estimate along scan x at every x shift u and detector column j.
+__global__ void obj_xsum_kernel(const float2* __restrict__ O, const float2* __restrict__ Ex,
+                                float2* __restrict__ T, int nu, int Sy, int Sx, int Nx) {
+    const int64_t total = (int64_t)nu * Sy * Nx;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t % Nx);
+        const int64_t r = t / Nx;
+        const int sy = (int)(r % Sy);
+        const int u = (int)(r / Sy);
+        const float2* o = O + (size_t)sy * Sx;
+        const float2* e = Ex + ((size_t)u * Nx + j) * Sx;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int sx = 0; sx < Sx; ++sx) acc = cfmaf(o[sx], e[sx], acc);
+        T[t] = acc;
+    }
+}
+
+// K[v][i][j] = Psi0(i, j) conj Psi_v(i, j) with Psi0(i, j) = sum_sy Ey0[i][sy] T0[sy][j] (the
+// object spectrum at detector pixel (i, j)) and Psi_v the same at the pixel moved by -q_v.
+__global__ void omega_kernel(float2* __restrict__ K, const float2* __restrict__ Ey,
+                             const float2* __restrict__ T, const float2* __restrict__ Ey0,
+                             const float2* __restrict__ T0, int Sy, int Sx, int Ny, int Nx,
+                             int64_t total) {
+    const int64_t npix = (int64_t)Ny * Nx;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t / npix);
+        const int e = (int)(t - (int64_t)v * npix);
+        const int i = e / Nx, j = e - (e / Nx) * Nx;
+        const int vy = v / Sx, vx = v - (v / Sx) * Sx;
+        const float2* ey0 = Ey0 + (size_t)i * Sy;
+        const float2* ey = Ey + ((size_t)vy * Ny + i) * Sy;
+        const float2* t0 = T0 + j;
+        const float2* tv = T + (size_t)vx * Sy * Nx + j;
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        for (int sy = 0; sy < Sy; ++sy) {
+            a = cfmaf(ey0[sy], t0[(size_t)sy * Nx], a);
+            b = cfmaf(ey[sy], tv[(size_t)sy * Nx], b);
+        }
+        K[t] = make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    }
+}
+
+// vmax[v] = max over plane v of |K|^2; one CTA per scan frequency.
+__global__ void __launch_bounds__(kOffThreads)
+plane_max_kernel(const float2* __restrict__ K, float* __restrict__ vmax, int npix) {
+    __shared__ float redf[kOffThreads / 32];
+    const float2* k = K + (size_t)blockIdx.x * npix;
+    float m = 0.f;
+    for (int e = threadIdx.x; e < npix; e += blockDim.x) {
+        const float2 w = k[e];
+        m = fmaxf(m, w.x * w.x + w.y * w.y);
+    }
+    m = block_max(m, redf);
+    if (threadIdx.x == 0) vmax[blockIdx.x] = m;
+}
+
+// K = conj(W_O) / (|W_O|^2 + eps_v) in place, eps_v = eps * vmax[v] (relative, per frequency) or
+// eps (absolute); inactive frequencies and planes that are zero everywhere get 0.
+__global__ void wiener_pf_kernel(float2* __restrict__ K, const uint8_t* __restrict__ mask,
+                                 const float* __restrict__ vmax, int64_t npix, int64_t total,
+                                 float eps, int absolute) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t / npix);
+        const float2 w = K[t];
+        if (!mask[v]) {
+            K[t] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const float ev = absolute ? eps : eps * vmax[v];
+        const float d = w.x * w.x + w.y * w.y + ev;
+        K[t] = d > 0.f ? make_float2(w.x / d, -w.y / d) : make_float2(0.f, 0.f);
+    }
+}
+
+// dst[y][x] = src[-y][-x] (indices mod Sy, Sx), with its phase: the probe IFFT2(conj(p / sqrt(p_0)))
+// from the conjugated inverse DFT conj(IFFT2(p / sqrt(p_0))) that the object path computes.
+__global__ void negate_index_kernel(const float2* __restrict__ src, float2* __restrict__ dst,
+                                    float* __restrict__ phase, int Sy, int Sx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Sy * Sx) return;
+    const int y = t / Sx, x = t - (t / Sx) * Sx;
+    const int sy = y ? Sy - y : 0, sx = x ? Sx - x : 0;
+    const float2 val = src[(size_t)sy * Sx + sx];
+    dst[t] = val;
+    if (phase) phase[t] = atan2f(val.y, val.x);
 }
 
 // ---- four-step transforms: a 1-D transform of n = N1 N2 points as N2 register DFTs of N1
@@ -981,6 +1112,11 @@ int64_t offline_planned_bytes(const wdd_offline_plan* P) {
     b += (int64_t)P->S * (1 + 8 + 8) + 8 * (int64_t)(P->Sy + P->Sx);
     b += 8 * (int64_t)(2 * P->Sy + 2 * P->Sx + P->Ny + P->Nx);
     if (!P->fused) b += (int64_t)P->S * P->ncb * 8;
+    if (P->swapped)
+        b += 8 * ((int64_t)P->Sy * P->Ny * P->Sy + (int64_t)P->Ny * P->Sy +
+                  (int64_t)P->Sx * P->Nx * P->Sx + (int64_t)P->Nx * P->Sx +
+                  (int64_t)P->Sx * P->Sy * P->Nx + (int64_t)P->Sy * P->Nx) +
+             4 * (int64_t)P->S;
     return b + 4;
 }
 
@@ -1004,7 +1140,11 @@ void off_release(wdd_offline_plan* P) {
     P->allocs.clear();
 }
 
-wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, int64_t* footprint) {
+// obj != NULL builds the plan of the swapped deconvolution (probe reconstruction, Sect. 10)
+// from that object estimate: complex64 [Sy][Sx], device or pinned host memory, read during the
+// call only.
+wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, int64_t* footprint,
+                               const void* obj) {
     if (!prm || !out) return off_fail(WDD_ERR_INVALID_ARG, "params or out is NULL");
     *out = nullptr;
     const wdd_params& p = *prm;
@@ -1023,6 +1163,10 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
         return off_fail(WDD_ERR_INVALID_ARG, "unknown frame dtype");
     if (!std::isfinite(p.scan_rotation_rad))
         return off_fail(WDD_ERR_INVALID_ARG, "scan_rotation_rad must be finite");
+    if (obj && p.scan_rotation_rad != 0.0)
+        return off_fail(WDD_ERR_UNSUPPORTED,
+                        "probe reconstruction on the GPU takes the object spectrum one scan axis "
+                        "at a time: scan_rotation_rad must be 0");
     const bool cy_default = p.det_center_y < 0 || p.det_center_y == (double)(p.det_y / 2);
     const bool cx_default = p.det_center_x < 0 || p.det_center_x == (double)(p.det_x / 2);
     if (!cy_default || !cx_default)
@@ -1042,6 +1186,7 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
     P->rb = rows_per_cta(P->Nx);
     P->cp = cols_per_cta(P->Ny);
     P->ncb = (P->Nx + P->cp - 1) / P->cp;
+    P->swapped = obj ? 1 : 0;
     P->lambda = electron_wavelength(p.voltage_v);
     P->R = p.semiconv_rad / (P->lambda * p.det_px_inv_m);
     std::vector<double> qy, qx;
@@ -1060,6 +1205,23 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
         std::snprintf(buf, sizeof buf, "classical plan needs %lld bytes, budget is %lld",
                       (long long)need, (long long)p.hbm_budget_bytes);
         return off_fail(WDD_ERR_OUT_OF_MEMORY, buf);
+    }
+    const float2* O = nullptr;  // the object estimate as a device address (swapped plan)
+    if (obj) {
+        cudaPointerAttributes attr{};
+        if (cudaPointerGetAttributes(&attr, obj) != cudaSuccess) {
+            cudaGetLastError();
+            attr.type = cudaMemoryTypeUnregistered;
+        }
+        if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+            O = static_cast<const float2*>(obj);
+        else if (attr.type == cudaMemoryTypeHost)
+            O = static_cast<const float2*>(attr.devicePointer ? attr.devicePointer : obj);
+        if (!O) {
+            delete P;
+            return off_fail(WDD_ERR_INVALID_ARG,
+                            "object estimate must be in device or pinned host memory");
+        }
     }
     {
         cudaError_t pe = prepare_offline_kernels();
@@ -1091,6 +1253,15 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
     WDD_OFF_ALLOC(P->d_tmp, P->S);
     WDD_OFF_ALLOC(P->d_max, 1);
     if (!P->fused) WDD_OFF_ALLOC(P->d_part, (size_t)P->S * P->ncb);
+    if (P->swapped) {
+        WDD_OFF_ALLOC(P->d_Ey, (size_t)P->Sy * P->Ny * P->Sy);
+        WDD_OFF_ALLOC(P->d_Ey0, (size_t)P->Ny * P->Sy);
+        WDD_OFF_ALLOC(P->d_Ex, (size_t)P->Sx * P->Nx * P->Sx);
+        WDD_OFF_ALLOC(P->d_Ex0, (size_t)P->Nx * P->Sx);
+        WDD_OFF_ALLOC(P->d_T, (size_t)P->Sx * P->Sy * P->Nx);
+        WDD_OFF_ALLOC(P->d_T0, (size_t)P->Sy * P->Nx);
+        WDD_OFF_ALLOC(P->d_vmax, P->S);
+    }
 #undef WDD_OFF_ALLOC
 
     cudaStream_t s0 = nullptr;
@@ -1113,13 +1284,60 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
     tw(P->d_tw_dx, P->Nx);
     if ((e = launch_idft_tables(P->d_twy_inv, P->Sy, P->d_twx_inv, P->Sx, s0))) return cbail(e, "tables");
 
+    const int64_t total = (int64_t)big;
+    const int ew_blocks = (int)std::min<int64_t>((total + kOffThreads - 1) / kOffThreads, 152 * 64);
+    if (P->swapped) {
+        // ---- Wiener kernel of the swapped deconvolution: Omega_v from the object estimate,
+        // W_O = IFFT2(ifftshift Omega_v), eps_v = epsilon max_r |W_O(v, r)|^2 per frequency,
+        // conj(W_O) / (|W_O|^2 + eps_v) ----
+        const double dks = p.det_px_inv_m * p.scan_step_m;
+        auto table = [&](float2* E, const double* q, int nv, int n, int ns, double c) {
+            const int64_t tot = (int64_t)nv * n * ns;
+            const int b = (int)std::min<int64_t>((tot + kOffThreads - 1) / kOffThreads, 152 * 64);
+            axis_dtft_table_kernel<<<b, kOffThreads, 0, s0>>>(E, q, nv, n, ns, c, dks);
+        };
+        auto xsum = [&](const float2* E, float2* T, int nu) {
+            const int64_t tot = (int64_t)nu * P->Sy * P->Nx;
+            const int b = (int)std::min<int64_t>((tot + kOffThreads - 1) / kOffThreads, 152 * 64);
+            obj_xsum_kernel<<<b, kOffThreads, 0, s0>>>(O, E, T, nu, P->Sy, P->Sx, P->Nx);
+        };
+        table(P->d_Ey, P->d_qy, P->Sy, P->Ny, P->Sy, (double)(P->Ny / 2));
+        table(P->d_Ey0, nullptr, 1, P->Ny, P->Sy, (double)(P->Ny / 2));
+        table(P->d_Ex, P->d_qx, P->Sx, P->Nx, P->Sx, (double)(P->Nx / 2));
+        table(P->d_Ex0, nullptr, 1, P->Nx, P->Sx, (double)(P->Nx / 2));
+        xsum(P->d_Ex, P->d_T, P->Sx);
+        xsum(P->d_Ex0, P->d_T0, 1);
+        omega_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(P->d_K, P->d_Ey, P->d_T, P->d_Ey0, P->d_T0,
+                                                        P->Sy, P->Sx, P->Ny, P->Nx, total);
+        if ((e = cudaGetLastError())) return cbail(e, "object autocorrelation");
+        if ((e = cudaMemset(P->d_max, 0, 4))) return cbail(e, "zero max");
+        if ((e = launch_detector<1>(P, P->d_K, s0))) return cbail(e, "object transform");
+        plane_max_kernel<<<P->S, kOffThreads, 0, s0>>>(P->d_K, P->d_vmax, P->npix);
+        if ((e = cudaGetLastError())) return cbail(e, "plane maxima");
+        unsigned maxbits = 0;
+        if ((e = cudaMemcpy(&maxbits, P->d_max, 4, cudaMemcpyDeviceToHost))) return cbail(e, "max");
+        float maxwo;
+        std::memcpy(&maxwo, &maxbits, 4);
+        P->eps_eff = p.eps_absolute ? p.epsilon : p.epsilon * (double)maxwo;
+        if (!(maxwo > 0)) {
+            off_release(P);
+            delete P;
+            return off_fail(WDD_ERR_INVALID_ARG, "object autocorrelation is zero everywhere");
+        }
+        wiener_pf_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(P->d_K, P->d_mask, P->d_vmax, P->npix,
+                                                            total, (float)p.epsilon,
+                                                            p.eps_absolute ? 1 : 0);
+        if ((e = cudaGetLastError())) return cbail(e, "Wiener kernel");
+        if ((e = cudaDeviceSynchronize())) return cbail(e, "probe plan build");
+        *out = P;
+        return WDD_OK;
+    }
+
     // ---- Wiener kernel: Y_v, W_P = IFFT2(ifftshift Y_v), eps_eff, conj(W_P) / (|W_P|^2 + eps) ----
     const double R2 = P->R * P->R;
     const double coef = 3.14159265358979323846 * P->lambda * p.defocus_m *
                         (p.det_px_inv_m * p.det_px_inv_m);
     const double rc = std::cos(p.scan_rotation_rad), rs = std::sin(p.scan_rotation_rad);
-    const int64_t total = (int64_t)big;
-    const int ew_blocks = (int)std::min<int64_t>((total + kOffThreads - 1) / kOffThreads, 152 * 64);
     probe_autocorr_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(
         P->d_K, P->d_qy, P->d_qx, P->Sx, P->Ny, P->Nx, (double)(P->Ny / 2), (double)(P->Nx / 2),
         R2, coef, rc, rs, total);
@@ -1150,13 +1368,22 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
 using namespace wdd;
 
 wdd_status wdd_offline_plan_create(const wdd_params* p, wdd_offline_plan** out) {
-    return offline_create_impl(p, out, nullptr);
+    return offline_create_impl(p, out, nullptr, nullptr);
+}
+
+wdd_status wdd_offline_probe_plan_create(const wdd_params* p, const void* obj,
+                                         wdd_offline_plan** out) {
+    if (!obj) {
+        if (out) *out = nullptr;
+        return off_fail(WDD_ERR_INVALID_ARG, "object estimate is NULL");
+    }
+    return offline_create_impl(p, out, nullptr, obj);
 }
 
 wdd_status wdd_offline_footprint(const wdd_params* p, int64_t* bytes) {
     if (!bytes) return off_fail(WDD_ERR_INVALID_ARG, "bytes is NULL");
     wdd_offline_plan* unused = nullptr;
-    return offline_create_impl(p, &unused, bytes);
+    return offline_create_impl(p, &unused, bytes, nullptr);
 }
 
 wdd_status wdd_offline_plan_destroy(wdd_offline_plan* P) {
@@ -1211,6 +1438,15 @@ wdd_status wdd_offline_reconstruct(wdd_offline_plan* P, const void* frames, wdd_
     if (e == cudaSuccess)
         e = launch_idft(P->d_o, P->d_twx_inv, P->d_twy_inv, P->d_tmp, P->Sy, P->Sx,
                         static_cast<float2*>(out->obj), out->phase, st);
+    // swapped plan: the probe IFFT2(conj(p / sqrt(p_0))) is that result at the negated index
+    if (e == cudaSuccess && P->swapped) {
+        e = cudaMemcpyAsync(P->d_tmp, out->obj, 8 * (size_t)P->S, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) {
+            negate_index_kernel<<<(P->S + kOffThreads - 1) / kOffThreads, kOffThreads, 0, st>>>(
+                P->d_tmp, static_cast<float2*>(out->obj), out->phase, P->Sy, P->Sx);
+            e = cudaGetLastError();
+        }
+    }
     if (e != cudaSuccess) return off_cuda_fail(e, "classical reconstruction");
     out->frames_seen = P->S;
     out->positions_covered = P->S;

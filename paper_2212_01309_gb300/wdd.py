@@ -110,6 +110,8 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "wdd_offline_plan_create": (ctypes.c_int, [ctypes.POINTER(Params),
                                                ctypes.POINTER(ctypes.c_void_p)]),
+    "wdd_offline_probe_plan_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p,
+                                                     ctypes.POINTER(ctypes.c_void_p)]),
     "wdd_offline_footprint": (ctypes.c_int, [ctypes.POINTER(Params),
                                              ctypes.POINTER(ctypes.c_int64)]),
     "wdd_offline_reconstruct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
@@ -371,16 +373,29 @@ def offline_footprint(params: Params) -> int:
 
 
 class OfflinePlan:
-    """Classical WDD on the whole 4-D dataset (wdd_offline_*): the comparison method, on the GPU."""
+    """Classical WDD on the whole 4-D dataset (wdd_offline_*): the comparison method, on the GPU.
 
-    def __init__(self, params: Params):
-        import torch  # noqa: F401  (device context, memory and streams)
+    With ``obj`` (complex64 [scan_y, scan_x] object estimate on the GPU) the plan runs the
+    deconvolution with the roles swapped (wdd_offline_probe_plan_create) and ``reconstruct``
+    returns the probe on the scan grid instead of the object."""
+
+    def __init__(self, params: Params, obj=None):
+        import torch
         self.params = params
-        h = ctypes.c_void_p()
-        _check(lib().wdd_offline_plan_create(ctypes.byref(params), ctypes.byref(h)),
-               "wdd_offline_plan_create")
-        self._h = h
         self.S = params.scan_y * params.scan_x
+        h = ctypes.c_void_p()
+        if obj is None:
+            _check(lib().wdd_offline_plan_create(ctypes.byref(params), ctypes.byref(h)),
+                   "wdd_offline_plan_create")
+        else:
+            if (not isinstance(obj, torch.Tensor) or obj.dtype != torch.complex64
+                    or obj.numel() != self.S or not obj.is_contiguous()):
+                raise ValueError("obj must be a contiguous complex64 tensor of scan_y * scan_x")
+            _check(lib().wdd_offline_probe_plan_create(ctypes.byref(params),
+                                                       ctypes.c_void_p(_ptr(obj)),
+                                                       ctypes.byref(h)),
+                   "wdd_offline_probe_plan_create")
+        self._h = h
 
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:

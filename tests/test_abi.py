@@ -148,6 +148,27 @@ def test_classical_plan_footprint_and_validation_without_gpu(wdd):
     assert L.wdd_offline_plan_destroy(None) == wdd.ERR_INVALID_ARG
 
 
+def test_probe_plan_validation_without_gpu(wdd):
+    """The probe-reconstruction plan (the swapped deconvolution) refuses a missing object
+    estimate and a rotated scan before touching the GPU."""
+    import numpy as np
+    kw = dict(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=32, det_x=32, det_px_inv_m=1e9,
+              voltage_v=3e5, semiconv_rad=0.02, rank_k=1)
+    L = wdd.lib()
+    h = ctypes.c_void_p(1)
+    p = wdd.make_params(**kw)
+    assert L.wdd_offline_probe_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == \
+        wdd.ERR_INVALID_ARG
+    assert h.value is None
+    est = np.ones(64, dtype=np.complex64)
+    rot = wdd.make_params(scan_rotation_rad=0.3, **kw)
+    assert L.wdd_offline_probe_plan_create(ctypes.byref(rot), ctypes.c_void_p(est.ctypes.data),
+                                           ctypes.byref(h)) == wdd.ERR_UNSUPPORTED
+    bad = wdd.make_params(**dict(kw, epsilon=-1.0))
+    assert L.wdd_offline_probe_plan_create(ctypes.byref(bad), ctypes.c_void_p(est.ctypes.data),
+                                           ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+
+
 def test_rotation_and_centre_validation_without_gpu(wdd):
     kw = dict(scan_y=8, scan_x=8, scan_step_m=1e-10, det_y=32, det_x=32, det_px_inv_m=1e9,
               voltage_v=3e5, semiconv_rad=0.02, rank_k=16)
