@@ -54,12 +54,13 @@ struct wdd_offline_plan {
     unsigned* d_max = nullptr;   // [1] max |W_P|^2 (float bits)
     // probe reconstruction (Sect. 10): K built from an object estimate instead of the probe
     int swapped = 0;
-    float2* d_Ey = nullptr;      // [Sy][Ny][Sy] scan-y sums at detector row i - cy - qy[vy]
-    float2* d_Ey0 = nullptr;     // [Ny][Sy] the same without the shift
-    float2* d_Ex = nullptr;      // [Sx][Nx][Sx]
-    float2* d_Ex0 = nullptr;     // [Nx][Sx]
-    float2* d_T = nullptr;       // [Sx][Sy][Nx] x sums of the object estimate per x shift
-    float2* d_T0 = nullptr;      // [Sy][Nx]
+    double2* d_Ey = nullptr;     // [Sy][Ny][Sy] scan-y sums at detector row i - cy - qy[vy]
+    double2* d_Ey0 = nullptr;    // [Ny][Sy] the same without the shift
+    double2* d_Ex = nullptr;     // [Sx][Nx][Sx]
+    double2* d_Ex0 = nullptr;    // [Nx][Sx]
+    double2* d_T = nullptr;      // [Sx][Sy][Nx] x sums of the object estimate per x shift
+    double2* d_T0 = nullptr;     // [Sy][Nx]
+    double2* d_Psi0 = nullptr;   // [Ny][Nx] object spectrum at the detector pixels
     float* d_vmax = nullptr;     // [S] max_r |W_O(v, r)|^2
     std::vector<wdd::DevBuf> allocs;
     int64_t device_bytes = 0;
@@ -96,10 +97,6 @@ __device__ __forceinline__ int brev_bits(int j, int logn) {
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ float2 cfmaf(float2 a, float2 b, float2 c) {  // c + a b
-    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 
 __device__ __forceinline__ float2 as_c(uint16_t v) { return make_float2((float)v, 0.f); }
@@ -482,13 +479,20 @@ __global__ void wiener_kernel(float2* __restrict__ K, const uint8_t* __restrict_
 // kernel is built from Omega_v(q) = Psi(q) conj Psi(q - q_v), Psi the spectrum of an object
 // estimate given on the scan grid, evaluated at detector-pixel frequencies as the trigonometric
 // sum over the scan positions.  Without a scan rotation that sum separates into one sum per
-// scan axis, which is what the tables below hold.
+// scan axis, which is what the tables below hold.  The sums run in FP64: away from its peaks
+// Psi is a small result of S unit-size terms, and FP32 sums left 1e-3 errors in the probe of a
+// weak phase object where FP64 sums leave 2e-7; Omega is rounded to FP32 once, for the
+// detector transform.
+
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // c + a b
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
 
 // E[(v * n + i) * ns + s] = exp(-2 pi i frac(((i - c - q[v]) * dks) * s)) for v < nv, i < n,
 // s < ns: one axis of the trigonometric sum at detector-pixel frequency i - c - q[v] (q == NULL:
-// no shift, nv = 1).  dks = dk * scan step; the phase is reduced to one turn in FP64.
-__global__ void axis_dtft_table_kernel(float2* __restrict__ E, const double* __restrict__ q, int nv,
-                                       int n, int ns, double c, double dks) {
+// no shift, nv = 1).  dks = dk * scan step; the phase is reduced to one turn.
+__global__ void axis_dtft_table_kernel(double2* __restrict__ E, const double* __restrict__ q,
+                                       int nv, int n, int ns, double c, double dks) {
     const int64_t total = (int64_t)nv * n * ns;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -501,14 +505,14 @@ __global__ void axis_dtft_table_kernel(float2* __restrict__ E, const double* __r
         const double f = ph - floor(ph);
         double sn, cs;
         sincospi(-2.0 * f, &sn, &cs);
-        E[t] = make_float2((float)cs, (float)sn);
+        E[t] = make_double2(cs, sn);
     }
 }
 
 // T[(u * Sy + sy) * Nx + j] = sum_sx O[sy][sx] Ex[(u * Nx + j) * Sx + sx] for u < nu: the sums of
 // the object estimate along scan x at every x shift u and detector column j.
-__global__ void obj_xsum_kernel(const float2* __restrict__ O, const float2* __restrict__ Ex,
-                                float2* __restrict__ T, int nu, int Sy, int Sx, int Nx) {
+__global__ void obj_xsum_kernel(const float2* __restrict__ O, const double2* __restrict__ Ex,
+                                double2* __restrict__ T, int nu, int Sy, int Sx, int Nx) {
     const int64_t total = (int64_t)nu * Sy * Nx;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -517,19 +521,32 @@ __global__ void obj_xsum_kernel(const float2* __restrict__ O, const float2* __re
         const int sy = (int)(r % Sy);
         const int u = (int)(r / Sy);
         const float2* o = O + (size_t)sy * Sx;
-        const float2* e = Ex + ((size_t)u * Nx + j) * Sx;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int sx = 0; sx < Sx; ++sx) acc = cfmaf(o[sx], e[sx], acc);
+        const double2* e = Ex + ((size_t)u * Nx + j) * Sx;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int sx = 0; sx < Sx; ++sx) {
+            const float2 ov = o[sx];
+            acc = cfma(make_double2(ov.x, ov.y), e[sx], acc);
+        }
         T[t] = acc;
     }
 }
 
-// K[v][i][j] = Psi0(i, j) conj Psi_v(i, j) with Psi0(i, j) = sum_sy Ey0[i][sy] T0[sy][j] (the
-// object spectrum at detector pixel (i, j)) and Psi_v the same at the pixel moved by -q_v.
-__global__ void omega_kernel(float2* __restrict__ K, const float2* __restrict__ Ey,
-                             const float2* __restrict__ T, const float2* __restrict__ Ey0,
-                             const float2* __restrict__ T0, int Sy, int Sx, int Ny, int Nx,
-                             int64_t total) {
+// Psi0[i][j] = sum_sy Ey0[i][sy] T0[sy][j]: the object spectrum at detector pixel (i, j).
+__global__ void psi0_kernel(const double2* __restrict__ Ey0, const double2* __restrict__ T0,
+                            double2* __restrict__ Psi0, int Sy, int Ny, int Nx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Ny * Nx) return;
+    const int i = t / Nx, j = t - (t / Nx) * Nx;
+    double2 a = make_double2(0.0, 0.0);
+    for (int sy = 0; sy < Sy; ++sy) a = cfma(Ey0[(size_t)i * Sy + sy], T0[(size_t)sy * Nx + j], a);
+    Psi0[t] = a;
+}
+
+// K[v][i][j] = Psi0[i][j] conj Psi_v(i, j), Psi_v(i, j) = sum_sy Ey[vy][i][sy] T[vx][sy][j]: the
+// object spectrum at the detector pixel moved by -q_v; rounded to complex64.
+__global__ void omega_kernel(float2* __restrict__ K, const double2* __restrict__ Ey,
+                             const double2* __restrict__ T, const double2* __restrict__ Psi0,
+                             int Sy, int Sx, int Ny, int Nx, int64_t total) {
     const int64_t npix = (int64_t)Ny * Nx;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -537,16 +554,12 @@ __global__ void omega_kernel(float2* __restrict__ K, const float2* __restrict__ 
         const int e = (int)(t - (int64_t)v * npix);
         const int i = e / Nx, j = e - (e / Nx) * Nx;
         const int vy = v / Sx, vx = v - (v / Sx) * Sx;
-        const float2* ey0 = Ey0 + (size_t)i * Sy;
-        const float2* ey = Ey + ((size_t)vy * Ny + i) * Sy;
-        const float2* t0 = T0 + j;
-        const float2* tv = T + (size_t)vx * Sy * Nx + j;
-        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-        for (int sy = 0; sy < Sy; ++sy) {
-            a = cfmaf(ey0[sy], t0[(size_t)sy * Nx], a);
-            b = cfmaf(ey[sy], tv[(size_t)sy * Nx], b);
-        }
-        K[t] = make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+        const double2* ey = Ey + ((size_t)vy * Ny + i) * Sy;
+        const double2* tv = T + (size_t)vx * Sy * Nx + j;
+        double2 b = make_double2(0.0, 0.0);
+        for (int sy = 0; sy < Sy; ++sy) b = cfma(ey[sy], tv[(size_t)sy * Nx], b);
+        const double2 a = Psi0[e];
+        K[t] = make_float2((float)(a.x * b.x + a.y * b.y), (float)(a.y * b.x - a.x * b.y));
     }
 }
 
@@ -1113,9 +1126,10 @@ int64_t offline_planned_bytes(const wdd_offline_plan* P) {
     b += 8 * (int64_t)(2 * P->Sy + 2 * P->Sx + P->Ny + P->Nx);
     if (!P->fused) b += (int64_t)P->S * P->ncb * 8;
     if (P->swapped)
-        b += 8 * ((int64_t)P->Sy * P->Ny * P->Sy + (int64_t)P->Ny * P->Sy +
-                  (int64_t)P->Sx * P->Nx * P->Sx + (int64_t)P->Nx * P->Sx +
-                  (int64_t)P->Sx * P->Sy * P->Nx + (int64_t)P->Sy * P->Nx) +
+        b += 16 * ((int64_t)P->Sy * P->Ny * P->Sy + (int64_t)P->Ny * P->Sy +
+                   (int64_t)P->Sx * P->Nx * P->Sx + (int64_t)P->Nx * P->Sx +
+                   (int64_t)P->Sx * P->Sy * P->Nx + (int64_t)P->Sy * P->Nx +
+                   (int64_t)P->Ny * P->Nx) +
              4 * (int64_t)P->S;
     return b + 4;
 }
@@ -1260,6 +1274,7 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
         WDD_OFF_ALLOC(P->d_Ex0, (size_t)P->Nx * P->Sx);
         WDD_OFF_ALLOC(P->d_T, (size_t)P->Sx * P->Sy * P->Nx);
         WDD_OFF_ALLOC(P->d_T0, (size_t)P->Sy * P->Nx);
+        WDD_OFF_ALLOC(P->d_Psi0, (size_t)P->Ny * P->Nx);
         WDD_OFF_ALLOC(P->d_vmax, P->S);
     }
 #undef WDD_OFF_ALLOC
@@ -1291,12 +1306,12 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
         // W_O = IFFT2(ifftshift Omega_v), eps_v = epsilon max_r |W_O(v, r)|^2 per frequency,
         // conj(W_O) / (|W_O|^2 + eps_v) ----
         const double dks = p.det_px_inv_m * p.scan_step_m;
-        auto table = [&](float2* E, const double* q, int nv, int n, int ns, double c) {
+        auto table = [&](double2* E, const double* q, int nv, int n, int ns, double c) {
             const int64_t tot = (int64_t)nv * n * ns;
             const int b = (int)std::min<int64_t>((tot + kOffThreads - 1) / kOffThreads, 152 * 64);
             axis_dtft_table_kernel<<<b, kOffThreads, 0, s0>>>(E, q, nv, n, ns, c, dks);
         };
-        auto xsum = [&](const float2* E, float2* T, int nu) {
+        auto xsum = [&](const double2* E, double2* T, int nu) {
             const int64_t tot = (int64_t)nu * P->Sy * P->Nx;
             const int b = (int)std::min<int64_t>((tot + kOffThreads - 1) / kOffThreads, 152 * 64);
             obj_xsum_kernel<<<b, kOffThreads, 0, s0>>>(O, E, T, nu, P->Sy, P->Sx, P->Nx);
@@ -1307,7 +1322,9 @@ wdd_status offline_create_impl(const wdd_params* prm, wdd_offline_plan** out, in
         table(P->d_Ex0, nullptr, 1, P->Nx, P->Sx, (double)(P->Nx / 2));
         xsum(P->d_Ex, P->d_T, P->Sx);
         xsum(P->d_Ex0, P->d_T0, 1);
-        omega_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(P->d_K, P->d_Ey, P->d_T, P->d_Ey0, P->d_T0,
+        psi0_kernel<<<(P->npix + kOffThreads - 1) / kOffThreads, kOffThreads, 0, s0>>>(
+            P->d_Ey0, P->d_T0, P->d_Psi0, P->Sy, P->Ny, P->Nx);
+        omega_kernel<<<ew_blocks, kOffThreads, 0, s0>>>(P->d_K, P->d_Ey, P->d_T, P->d_Psi0,
                                                         P->Sy, P->Sx, P->Ny, P->Nx, total);
         if ((e = cudaGetLastError())) return cbail(e, "object autocorrelation");
         if ((e = cudaMemset(P->d_max, 0, 4))) return cbail(e, "zero max");
