@@ -152,6 +152,20 @@ wdd_status wdd_plan_footprint(const wdd_params* p, int64_t* bytes);
 /* Releases every device and host buffer of the plan (synchronises with its last stream). */
 wdd_status wdd_plan_destroy(wdd_plan* plan);
 
+/* Wiener filter update from a recovered probe (Sect. 10): rebuilds chi_v, eps_eff and the
+ * weights of Algorithm 1 with Y_v(q) = A(q) conj A(q + q_v), A(k) = [|k| <= theta / lambda]
+ * exp(i arg P(k)), P(k) = sum_s probe_s exp(-2 pi i dk k . r_s) the spectrum of `probe` at
+ * detector-pixel frequencies: the condenser aperture is kept, the recovered probe gives the
+ * phase inside it.  `probe` is complex64 [scan_y][scan_x] on the scan grid with its origin at
+ * index 0 (the out->obj of wdd_offline_reconstruct on a probe plan), in device or pinned host
+ * memory, read during the call only.  The accumulator and the counters are kept, so the next
+ * snapshot deconvolves every frame pushed so far with the updated filter.  Synchronous: waits
+ * for all queued device work first and returns when the weights are rebuilt.  Errors:
+ * INVALID_ARG (NULL or pageable probe, an autocorrelation that is zero everywhere),
+ * UNSUPPORTED (scan_rotation_rad != 0, bases too large), STATE (finalized plan),
+ * OUT_OF_MEMORY, CUDA; on an error after the weights were started they are undefined. */
+wdd_status wdd_plan_set_probe(wdd_plan* plan, const void* probe);
+
 /* Streams n frames into the plan (the loop body of Algorithm 2).
  *  frames    n x det_y x det_x elements of frame_dtype, row-major, zero frequency at
  *            (det_center_y, det_center_x) (i.e. fftshifted).  Device memory, pinned host memory

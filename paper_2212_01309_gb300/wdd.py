@@ -88,6 +88,7 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
     "wdd_plan_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
     "wdd_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "wdd_plan_set_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "wdd_plan_footprint": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64)]),
     "wdd_flush": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_push_frames": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -289,6 +290,18 @@ class Plan:
         if stream is not None:
             self.set_stream(stream)
         return self._result(lib().wdd_finalize, obj, phase)
+
+    def set_probe(self, probe) -> None:
+        """Rebuilds the Wiener filter from a recovered probe (complex64 [scan_y, scan_x] on the
+        scan grid, e.g. the output of OfflinePlan(params, obj=...).reconstruct); the
+        accumulated frames are kept."""
+        import torch
+        if (not isinstance(probe, torch.Tensor) or probe.dtype != torch.complex64
+                or probe.numel() != self.params.scan_y * self.params.scan_x
+                or not probe.is_contiguous()):
+            raise ValueError("probe must be a contiguous complex64 tensor of scan_y * scan_x")
+        _check(lib().wdd_plan_set_probe(self._h, ctypes.c_void_p(_ptr(probe))),
+               "wdd_plan_set_probe")
 
     def flush(self, stream=None) -> None:
         """Accumulates the staged frames now (a later snapshot then only reconstructs)."""

@@ -167,6 +167,8 @@ def test_probe_plan_validation_without_gpu(wdd):
     bad = wdd.make_params(**dict(kw, epsilon=-1.0))
     assert L.wdd_offline_probe_plan_create(ctypes.byref(bad), ctypes.c_void_p(est.ctypes.data),
                                            ctypes.byref(h)) == wdd.ERR_INVALID_ARG
+    # the Wiener update of a live plan from a recovered probe
+    assert L.wdd_plan_set_probe(None, ctypes.c_void_p(est.ctypes.data)) == wdd.ERR_INVALID_ARG
 
 
 def test_rotation_and_centre_validation_without_gpu(wdd):
