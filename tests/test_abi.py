@@ -41,6 +41,12 @@ def test_library_exports_every_declared_symbol(wdd):
     assert set(wdd.exported_symbols()) >= set(declared_functions())
 
 
+def test_library_resolves_every_symbol_at_load(wdd):
+    """A shared library links with undefined symbols; binding them all at load time catches an
+    internal function that no translation unit defines."""
+    ctypes.CDLL(wdd.LIB_PATH, mode=os.RTLD_NOW)
+
+
 def test_status_strings(wdd):
     L = wdd.lib()
     assert L.wdd_status_string(0) == b"WDD_OK"
