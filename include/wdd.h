@@ -159,11 +159,12 @@ wdd_status wdd_plan_destroy(wdd_plan* plan);
  * phase inside it.  `probe` is complex64 [scan_y][scan_x] on the scan grid with its origin at
  * index 0 (the out->obj of wdd_offline_reconstruct on a probe plan), in device or pinned host
  * memory, read during the call only.  The accumulator and the counters are kept, so the next
- * snapshot deconvolves every frame pushed so far with the updated filter.  Synchronous: waits
- * for all queued device work first and returns when the weights are rebuilt.  Errors:
- * INVALID_ARG (NULL or pageable probe, an autocorrelation that is zero everywhere),
- * UNSUPPORTED (scan_rotation_rad != 0, bases too large), STATE (finalized plan),
- * OUT_OF_MEMORY, CUDA; on an error after the weights were started they are undefined. */
+ * snapshot deconvolves every frame pushed so far with the updated filter; this includes a
+ * finalized plan, whose acquisition is complete (wdd_snapshot still reconstructs it).
+ * Synchronous: waits for all queued device work first and returns when the weights are
+ * rebuilt.  Errors: INVALID_ARG (NULL or pageable probe, an autocorrelation that is zero
+ * everywhere), UNSUPPORTED (scan_rotation_rad != 0, bases too large), OUT_OF_MEMORY, CUDA; on
+ * an error after the weights were started they are undefined. */
 wdd_status wdd_plan_set_probe(wdd_plan* plan, const void* probe);
 
 /* Streams n frames into the plan (the loop body of Algorithm 2).

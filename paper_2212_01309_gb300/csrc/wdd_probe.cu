@@ -233,7 +233,6 @@ wdd_status wdd_plan_set_probe(wdd_plan* P, const void* probe) {
         return pfail(WDD_ERR_UNSUPPORTED,
                      "the probe update takes the probe spectrum one scan axis at a time: "
                      "scan_rotation_rad must be 0");
-    if (P->finished) return pfail(WDD_ERR_STATE, "plan is finalized");
     cudaPointerAttributes attr{};
     if (cudaPointerGetAttributes(&attr, probe) != cudaSuccess) {
         cudaGetLastError();
