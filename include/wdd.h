@@ -42,7 +42,7 @@ typedef enum {
     WDD_ERR_SCAN_INDEX = 4,    /* a scan index is outside [0, scan_y * scan_x) */
     WDD_ERR_STATE = 5,         /* push after finalize, or use of a destroyed plan */
     WDD_ERR_TIMEOUT = 6,       /* a bounded wait gave up */
-    WDD_ERR_UNSUPPORTED = 7    /* a valid request this build cannot serve (sizes, basis, dtype) */
+    WDD_ERR_UNSUPPORTED = 7    /* a valid request the library cannot serve (sizes, basis, dtype) */
 } wdd_status;
 
 /* Reduced detector bases.
