@@ -302,6 +302,18 @@ wdd_status wdd_reconstruct_noalloc(const void* weights, const void* accum, int32
 /* Copies the per-position hit counts (uint32 [S], exact host bookkeeping) into host memory. */
 wdd_status wdd_get_hit_counts(const wdd_plan* plan, uint32_t* host_out, int64_t n);
 
+/* Adds an exported state to the plan (checkpoint/resume and partition merge): Eq. 14 is linear
+ * in the frames, so the accumulator of a set of frames is the sum of the accumulators of any
+ * partition of it (the merge by summation of Sect. 6.3).  accum: complex64 [S][K] in any memory
+ * (read with wdd_copy_array(WDD_ARRAY_ACCUM) from a plan with the same parameters); hits: host
+ * uint32 [S] (wdd_get_hit_counts), summing to frames_seen.  Adds accum to the accumulator, hits
+ * to the hit counters and frames_seen to the frame count; merged into a freshly created (or
+ * reset) plan it resumes the acquisition exactly.  Synchronous (waits for queued device work).
+ * Errors: INVALID_ARG (NULL pointers, hits that do not add up to frames_seen, a counter that
+ * would overflow), OUT_OF_MEMORY (scratch copy), CUDA. */
+wdd_status wdd_merge_state(wdd_plan* plan, const void* accum, const uint32_t* hits,
+                           int64_t frames_seen);
+
 /* Internal arrays that wdd_copy_array can read back (tests and diagnostics). */
 typedef enum {
     WDD_ARRAY_WEIGHTS = 0,   /* complex64 [S][K]   W_v[k] (zero rows for inactive v)           */

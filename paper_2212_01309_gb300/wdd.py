@@ -89,6 +89,8 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
     "wdd_plan_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]),
     "wdd_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_plan_set_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "wdd_merge_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int64]),
     "wdd_plan_footprint": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64)]),
     "wdd_flush": (ctypes.c_int, [ctypes.c_void_p]),
     "wdd_push_frames": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -346,6 +348,22 @@ class Plan:
         _check(lib().wdd_get_hit_counts(self._h, ctypes.c_void_p(out.ctypes.data), self.S),
                "wdd_get_hit_counts")
         return out
+
+    def export_state(self) -> dict:
+        """The plan's state (accumulator with staged frames accumulated first, hit counters,
+        frame count): enough to resume the acquisition or merge it with another partition."""
+        return {"accum": self.copy_array("accum"), "hits": self.hit_counts(),
+                "frames_seen": int(self.info()["frames_seen"])}
+
+    def merge_state(self, state: dict) -> None:
+        """Adds an exported state (of a plan with the same parameters) to this plan."""
+        accum = np.ascontiguousarray(state["accum"], dtype=np.complex64)
+        hits = np.ascontiguousarray(state["hits"], dtype=np.uint32)
+        if accum.size != self.S * self.K or hits.size != self.S:
+            raise ValueError("state of a plan with other parameters")
+        _check(lib().wdd_merge_state(self._h, ctypes.c_void_p(accum.ctypes.data),
+                                     ctypes.c_void_p(hits.ctypes.data),
+                                     int(state["frames_seen"])), "wdd_merge_state")
 
     def copy_array(self, which: str) -> np.ndarray:
         inf = self.info()

@@ -175,6 +175,8 @@ def test_probe_plan_validation_without_gpu(wdd):
                                            ctypes.byref(h)) == wdd.ERR_INVALID_ARG
     # the Wiener update of a live plan from a recovered probe
     assert L.wdd_plan_set_probe(None, ctypes.c_void_p(est.ctypes.data)) == wdd.ERR_INVALID_ARG
+    # merging an exported state
+    assert L.wdd_merge_state(None, None, None, 0) == wdd.ERR_INVALID_ARG
 
 
 def test_rotation_and_centre_validation_without_gpu(wdd):
