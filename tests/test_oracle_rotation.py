@@ -118,3 +118,36 @@ def test_quarter_turns_in_classical_wdd(turns):
     # without the rotation the turned frames give another spectrum (compared without the
     # dominant v = 0 term)
     assert W.complex_rel_l2(W.offline_wdd(Fr, p0)[1:], o0[1:]) > 1e-2
+
+
+@pytest.mark.parametrize("turns", [1, 3])
+def test_quarter_turns_in_the_probe_swap(turns):
+    """The identity through the swapped deconvolution (Sect. 10, readings R17-R19): the object
+    estimate's spectrum is taken along the rotated scan axes, so the turned frames with the
+    rotated scan return the probe spectrum of the original frames."""
+    acq = odd_acq(defocus_m=5e-9)
+    F = synth.all_frames(acq)
+    p0 = W.Params.from_acquisition(acq, basis="fourier_full", rank_k=acq.det * acq.det,
+                                   epsilon=1e-3)
+    obj, _ = W.finalize(W.offline_wdd(F, p0), p0)
+    pv0 = W.offline_probe_wdd(F, obj, p0)
+    Fr = np.ascontiguousarray(np.rot90(F, k=turns, axes=(1, 2)))
+    pr = dataclasses.replace(p0, scan_rotation_rad=turns * math.pi / 2)
+    assert W.complex_rel_l2(W.offline_probe_wdd(Fr, obj, pr), pv0) < 1e-9
+    assert W.complex_rel_l2(W.offline_probe_wdd(Fr, obj, p0)[1:], pv0[1:]) > 1e-2
+
+
+def test_wrong_rotation_of_the_estimate_spectrum_is_caught(monkeypatch):
+    """A planted mistake: the object estimate's spectrum taken along axes turned by -theta."""
+    acq = odd_acq(defocus_m=5e-9)
+    F = synth.all_frames(acq)
+    p0 = W.Params.from_acquisition(acq, basis="fourier_full", rank_k=acq.det * acq.det,
+                                   epsilon=1e-3)
+    obj, _ = W.finalize(W.offline_wdd(F, p0), p0)
+    pv0 = W.offline_probe_wdd(F, obj, p0)
+    Fr = np.ascontiguousarray(np.rot90(F, k=1, axes=(1, 2)))
+    pr = dataclasses.replace(p0, scan_rotation_rad=math.pi / 2)
+    orig = W.scan_grid_spectrum_at
+    monkeypatch.setattr(W, "scan_grid_spectrum_at", lambda X, p, ky, kx: orig(
+        X, dataclasses.replace(p, scan_rotation_rad=-p.scan_rotation_rad), ky, kx))
+    assert W.complex_rel_l2(W.offline_probe_wdd(Fr, obj, pr)[1:], pv0[1:]) > 1e-2
