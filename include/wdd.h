@@ -304,13 +304,17 @@ wdd_status wdd_get_hit_counts(const wdd_plan* plan, uint32_t* host_out, int64_t 
 
 /* Adds an exported state to the plan (checkpoint/resume and partition merge): Eq. 14 is linear
  * in the frames, so the accumulator of a set of frames is the sum of the accumulators of any
- * partition of it (the merge by summation of Sect. 6.3).  accum: complex64 [S][K] in any memory
- * (read with wdd_copy_array(WDD_ARRAY_ACCUM) from a plan with the same parameters); hits: host
- * uint32 [S] (wdd_get_hit_counts), summing to frames_seen.  Adds accum to the accumulator, hits
- * to the hit counters and frames_seen to the frame count; merged into a freshly created (or
- * reset) plan it resumes the acquisition exactly.  Synchronous (waits for queued device work).
- * Errors: INVALID_ARG (NULL pointers, hits that do not add up to frames_seen, a counter that
- * would overflow), OUT_OF_MEMORY (scratch copy), CUDA. */
+ * partition of it (the merge by summation of Sect. 6.3).  accum: complex64 [S][K] in device or
+ * pinned host memory (read with wdd_copy_array(WDD_ARRAY_ACCUM) from a plan with the same
+ * parameters), borrowed until the plan's stream has passed the merge; hits: host uint32 [S]
+ * (wdd_get_hit_counts), summing to frames_seen, read before the call returns.  Adds accum to the
+ * accumulator (one kernel enqueued on the plan's last stream, after everything the plan has
+ * enqueued; nothing is allocated and nothing else is waited for), hits to the hit counters and
+ * frames_seen to the frame count; merged into a freshly created (or reset) plan it resumes the
+ * acquisition exactly.  Errors: INVALID_ARG (NULL pointers, pageable accum, a negative
+ * frames_seen, hits that do not add up to frames_seen, a counter that would overflow), STATE (a
+ * finalized plan: wdd_reset it first), CUDA; on an error nothing is enqueued and the counters
+ * are unchanged. */
 wdd_status wdd_merge_state(wdd_plan* plan, const void* accum, const uint32_t* hits,
                            int64_t frames_seen);
 

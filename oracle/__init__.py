@@ -11,9 +11,10 @@ Modules
               overlap criterion (Sect. 6.2, Eq. 15-17).
 
 Pins: tests/test_oracle_pins.py checks every function against values the paper prints, closed
-forms, library routines, brute force and exact invariants, and tests/test_oracle_mutations.py
-plants plausible mistakes and checks that the pins catch them.  One quantity has no independent
-pin: the absolute amplitude scale of the reconstructed object (the division by sqrt(o_0) in
-``finalize``), so its parity is unpinned; only the phase is graded.
+forms, library routines, brute force and exact invariants; tests/test_oracle_mutations.py
+plants plausible mistakes and checks that the pins catch them; tests/test_oracle_probe.py pins
+the amplitude scale as well (on a noiseless periodic forward model classical and live WDD return
+the object itself, unit scale included) and the probe reconstruction of Sect. 10.  The
+reconstruction quality of the Hermite-Gauss bases against ground truth has no independent pin.
 """
 from .wdd_oracle import *  # noqa: F401,F403

@@ -256,7 +256,7 @@ wdd_status wdd_plan_set_probe(wdd_plan* P, const void* probe) {
     const int Sy = P->Sy, Sx = P->Sx, Ny = P->Ny, Nx = P->Nx;
     TempBufs tmp;
     double2 *Ey = nullptr, *Ey0 = nullptr, *Ex = nullptr, *Ex0 = nullptr, *T = nullptr, *T0 = nullptr,
-            *A0 = nullptr, *chi = P->d_chi;
+            *A0 = nullptr, *chi = nullptr;
     uint8_t* d_used = nullptr;
     unsigned long long* d_max = nullptr;
     if (!e) e = tmp.get(&Ey, (size_t)Sy * Ny * Sy);
@@ -268,7 +268,9 @@ wdd_status wdd_plan_set_probe(wdd_plan* P, const void* probe) {
     if (!e) e = tmp.get(&A0, (size_t)Ny * Nx);
     if (!e) e = tmp.get(&d_used, (size_t)P->M);
     if (!e) e = tmp.get(&d_max, 1);
-    if (!e && !chi) e = tmp.get(&chi, (size_t)P->S * P->M);
+    // chi is built in a buffer of its own and replaces the plan's copy only once the update
+    // has succeeded, so a refused update leaves WDD_ARRAY_CHI as it was
+    if (!e) e = tmp.get(&chi, (size_t)P->S * P->M);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return pfail(WDD_ERR_OUT_OF_MEMORY, std::string("probe update buffers: ") + cudaGetErrorString(e));
@@ -327,6 +329,9 @@ wdd_status wdd_plan_set_probe(wdd_plan* P, const void* probe) {
     P->d_chi = chi;
     P->eps_eff = eps_eff;
     e = launch_weights(P, st);
+    if (!e && keep_chi)
+        e = cudaMemcpyAsync(keep_chi, chi, sizeof(double2) * (size_t)P->S * P->M,
+                            cudaMemcpyDeviceToDevice, st);
     if (!e) e = cudaDeviceSynchronize();
     P->d_chi = keep_chi;
     if (e != cudaSuccess) {

@@ -5,7 +5,8 @@ the device, each with its own plan (Wiener filter and accumulator in HBM) and CU
 batches arrive over time.  The loop:
 
   * admits waiting sessions first-fit whenever the HBM budget has room for their plan
-    (wdd_plan_footprint); a finished session's memory is returned and the next ones start;
+    (wdd_plan_footprint); a finished session's memory is returned and the next ones start; a
+    session whose plan alone exceeds the budget is refused (its frames are dropped) and counted;
   * coalesces each admitted session's contiguous pending batches into pushes on that session's
     stream, cut at its snapshot points, so the work of different sessions overlaps on the
     device;
@@ -103,6 +104,7 @@ class Server:
         self.latencies: list[tuple[float, int]] = []   # (seconds, frames)
         self.done_frames = 0
         self.admission_log: list[tuple[float, int, str]] = []
+        self.rejected: list[int] = []                   # sessions larger than the whole budget
 
     # ---- requests -----------------------------------------------------------------------
     def add_session(self, spec: Session) -> None:
@@ -119,6 +121,8 @@ class Server:
     def offer(self, sid: int, start: int, count: int, t_arrival: float | None = None) -> None:
         """Frames [start, start + count) of session sid have arrived."""
         t = self.clock() if t_arrival is None else t_arrival
+        if sid in self.rejected:
+            return
         if sid in self.live:
             self.live[sid].pending.append((t, start, count))
         else:
@@ -129,7 +133,12 @@ class Server:
         still = []
         for spec in self.waiting:
             need = self.footprint[spec.sid]
-            if self.budget is None or self.used + need <= self.budget or not self.live:
+            if self.budget is not None and need > self.budget:
+                # can never fit: refused outright rather than admitted over the budget
+                self.rejected.append(spec.sid)
+                self.backlog.pop(spec.sid, None)
+                self.admission_log.append((self.clock(), spec.sid, "reject"))
+            elif self.budget is None or self.used + need <= self.budget:
                 lv = _Live(spec, self.use_graphs)
                 self.live[spec.sid] = lv
                 self.used += need
@@ -247,4 +256,4 @@ class Server:
                 "frames_per_s": self.done_frames / wall_s if wall_s > 0 else 0.0,
                 "latency_p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "sessions": len(self.results)}
+                "sessions": len(self.results), "rejected": len(self.rejected)}

@@ -349,21 +349,39 @@ class Plan:
                "wdd_get_hit_counts")
         return out
 
+    def _signature(self) -> tuple:
+        p = self.params
+        return (p.scan_y, p.scan_x, p.det_y, p.det_x, p.rank_k, p.basis)
+
     def export_state(self) -> dict:
         """The plan's state (accumulator with staged frames accumulated first, hit counters,
         frame count): enough to resume the acquisition or merge it with another partition."""
         return {"accum": self.copy_array("accum"), "hits": self.hit_counts(),
-                "frames_seen": int(self.info()["frames_seen"])}
+                "frames_seen": int(self.info()["frames_seen"]), "signature": self._signature()}
 
-    def merge_state(self, state: dict) -> None:
-        """Adds an exported state (of a plan with the same parameters) to this plan."""
-        accum = np.ascontiguousarray(state["accum"], dtype=np.complex64)
-        hits = np.ascontiguousarray(state["hits"], dtype=np.uint32)
-        if accum.size != self.S * self.K or hits.size != self.S:
+    def merge_state(self, state: dict, stream=None) -> None:
+        """Adds an exported state (of a plan with the same parameters) to this plan, in stream
+        order.  ``state["accum"]`` may be a numpy array (copied to pinned memory here) or a
+        complex64 torch tensor on the GPU or in pinned memory."""
+        import torch
+        sig = state.get("signature")
+        if sig is not None and tuple(sig) != self._signature():
             raise ValueError("state of a plan with other parameters")
-        _check(lib().wdd_merge_state(self._h, ctypes.c_void_p(accum.ctypes.data),
+        accum = state["accum"]
+        if isinstance(accum, np.ndarray):
+            accum = torch.from_numpy(np.ascontiguousarray(accum, dtype=np.complex64)).pin_memory()
+        if accum.dtype != torch.complex64 or not accum.is_contiguous():
+            raise ValueError("accum must be contiguous complex64")
+        hits = np.ascontiguousarray(state["hits"], dtype=np.uint32)
+        if accum.numel() != self.S * self.K or hits.size != self.S:
+            raise ValueError("state of a plan with other parameters")
+        if stream is not None:
+            self.set_stream(stream)
+        _check(lib().wdd_merge_state(self._h, ctypes.c_void_p(_ptr(accum)),
                                      ctypes.c_void_p(hits.ctypes.data),
                                      int(state["frames_seen"])), "wdd_merge_state")
+        # borrowed until the stream has passed the merge
+        self._keep.append(accum)
 
     def copy_array(self, which: str) -> np.ndarray:
         inf = self.info()

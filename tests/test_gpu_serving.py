@@ -4,7 +4,10 @@ Each session's reconstruction must be the same whether it runs alone or in the m
 HBM budget forces sessions to queue, and whether snapshots replay captured CUDA graphs; the
 smallest session is also checked against the FP64 oracle.  Tolerance: the FP32 path's phase
 bound (1e-5 relative L2); in practice the results are bit-identical, because a session's frames
-are projected one by one and flushed only at its own snapshot points.
+are projected one by one and flushed only at its own snapshot points.  The FP32 path runs on an
+eighth-scale copy of the serving mix; the split tensor-core path runs on the half-scale mix
+(scans of 32 x 32 to 128 x 128 at the mix's full 64-256 pixel detectors, 54,272 frames), alone
+against in the mix, and its smallest session against the oracle within the split path's 2e-3.
 """
 import numpy as np
 import pytest
@@ -32,6 +35,24 @@ def mix():
         sessions.append((acq, rc, serving.Session(sid=sid, params=p, frames=frames,
                                                   n_frames=acq.n_frames)))
     arrivals = synth.serving_arrivals([a.n_frames for a, _, _ in sessions], seed=77)
+    return sessions, arrivals
+
+
+@pytest.fixture(scope="module")
+def mix_split():
+    import torch
+    from paper_2212_01309_gb300 import serving, wdd
+    from synth.torch_gen import TorchFrames
+    assert torch.cuda.is_available()
+    sessions = []
+    for sid, (acq, rc) in enumerate(synth.serving_mix(scale=2)):
+        frames = TorchFrames(acq).all()
+        p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                        epsilon=rc["epsilon"], max_batch=512, accum_depth=2048,
+                                        precision="split", coalesce_frames=1024)
+        sessions.append((acq, rc, serving.Session(sid=sid, params=p, frames=frames,
+                                                  n_frames=acq.n_frames)))
+    arrivals = synth.serving_arrivals([a.n_frames for a, _, _ in sessions], seed=78)
     return sessions, arrivals
 
 
@@ -114,3 +135,21 @@ def test_deadline_snapshots_open_loop(mix):
     p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
     _, ph = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
     assert phase_err(srv.results[0].astype(np.float64), ph) <= PHASE_TOL
+
+
+def test_split_path_alone_equals_mix(mix_split):
+    sessions, arrivals = mix_split
+    srv, stats = _serve(sessions, arrivals, snapshot_every=1024)
+    assert stats["sessions"] == len(sessions)
+    assert stats["frames"] == sum(a.n_frames for a, _, _ in sessions)
+    for sid, (acq, rc, s) in enumerate(sessions):
+        own = [(t, 0, st, c) for (t, q, st, c) in arrivals if q == sid]
+        alone, _ = _serve([(acq, rc, s)], [(t, s.sid, st, c) for (t, _, st, c) in own],
+                          snapshot_every=1024)
+        assert phase_err(srv.results[sid].astype(np.float64),
+                         alone.results[sid].astype(np.float64)) <= PHASE_TOL, sid
+    acq, rc, s = sessions[0]
+    frames = s.frames.cpu().numpy()
+    p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
+    _, ref = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
+    assert phase_err(srv.results[0].astype(np.float64), ref) <= 2e-3

@@ -31,3 +31,19 @@ def test_arrivals_cover_every_frame_in_raster_order():
     rate = sum(n) / arr[-1][0]
     assert 17000 < rate < 23000
     assert synth.serving_arrivals(n) == arr   # seeded
+
+
+def test_session_above_the_whole_budget_is_refused():
+    """Admission never goes over the HBM budget: a session whose plan alone exceeds it is
+    refused (and counted), not admitted because nothing else is live.  Host logic only: the
+    refused session never builds a plan."""
+    import pytest
+    wdd = pytest.importorskip("paper_2212_01309_gb300.wdd")
+    from paper_2212_01309_gb300 import serving
+    acq, rc = synth.serving_mix()[0]
+    p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"])
+    srv = serving.Server(hbm_budget_bytes=wdd.plan_footprint(p) - 1)
+    srv.add_session(serving.Session(sid=0, params=p, frames=None, n_frames=acq.n_frames))
+    stats = srv.run([(0.0, 0, 0, 64), (0.0, 0, 64, 64)], open_loop=False, timeout_s=5)
+    assert stats["rejected"] == 1 and stats["sessions"] == 0 and stats["frames"] == 0
+    assert srv.admission_log[0][1:] == (0, "reject") and not srv.live
