@@ -39,6 +39,7 @@ ACCUM_DEPTH = 4096     # frames staged per tensor-core accumulation on the optim
 COALESCE = 1024        # pushes gathered into projection launches of up to 1024 frames
 TIMING_REPLAYS = 3     # replays of the step captured with stage-timing events
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+EXEC_FACTOR = 3        # tensor-core products per algorithmic product on the split path
 
 
 def _env_int(name, default):
@@ -531,8 +532,8 @@ def main(argv=None) -> int:
     stage_ms = {k: v[0] for k, v in st.items()}
     dom = max(stage_ms, key=stage_ms.get)
     # launches per flush of the optimised path: the split pre-pass, then one accumulation launch
-    # per 1024 staged frames (the library's segment length)
-    per_flush = (1 + (ACCUM_DEPTH + 1023) // 1024) if path == "split" else 1
+    # (all TMEM segments of the flush)
+    per_flush = 2 if path == "split" else 1
     ms_launch = st[dom][0] / max(1, st[dom][1])
     if dom == "accumulate":
         ms_launch *= per_flush           # one flush of ACCUM_DEPTH frames
@@ -545,11 +546,13 @@ def main(argv=None) -> int:
                     "frac": ach / peaks["bf16"],
                     "traffic": (tr_a["bytes_per_launch"] * ACCUM_DEPTH / tr_a["frames_per_launch"])
                                if tr_a else None,
-                    "achieved_executed": 4 * ach, "frac_executed": 4 * ach / peaks["bf16"],
-                    "note": f"one flush of {ACCUM_DEPTH} frames (split pre-pass + "
-                            f"{per_flush - 1} launches); algorithmic 4*S*K flops per frame; the "
-                            f"split path executes 4x that (hi/lo of both operands); peak = "
-                            f"{peaks['src']} bf16 dense (fp16 same rate)"}
+                    "achieved_executed": EXEC_FACTOR * ach,
+                    "frac_executed": EXEC_FACTOR * ach / peaks["bf16"],
+                    "note": f"one flush of {ACCUM_DEPTH} frames (split pre-pass + one "
+                            f"accumulation launch); algorithmic 4*S*K flops per frame; the split "
+                            f"path executes {EXEC_FACTOR}x that (hi*hi, hi*lo, lo*hi of phase "
+                            f"factors and coefficients); peak = {peaks['src']} bf16 dense (fp16 "
+                            f"same rate)"}
         else:
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
@@ -580,19 +583,20 @@ def main(argv=None) -> int:
     acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1]) * per_flush   # per flush
     acc_alg = 4.0 * S * K * ACCUM_DEPTH / (acc_ms * 1e-3) / 1e12
     tr_acc = _traffic("accumulate_tc_kernel") if path == "split" else None
-    roof_acc = {"bound": "tensor", "kernel": f"split_coeff + {per_flush - 1} x accumulate_tc "
+    roof_acc = {"bound": "tensor", "kernel": f"split_coeff + accumulate_tc "
                 f"(one flush of {ACCUM_DEPTH} frames)" if path == "split"
                 else "accumulate_fp32", "flush_ms": acc_ms,
                 "traffic": (tr_acc["bytes_per_launch"] * ACCUM_DEPTH / tr_acc["frames_per_launch"])
                            if tr_acc else None,
-                "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * (4 if path == "split" else 1),
+                "achieved_algorithmic": acc_alg,
+                "achieved_executed": acc_alg * (EXEC_FACTOR if path == "split" else 1),
                 "peak": peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac_algorithmic": acc_alg / (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),
-                "frac_executed": acc_alg * (4 if path == "split" else 1) /
+                "frac_executed": acc_alg * (EXEC_FACTOR if path == "split" else 1) /
                                  (peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS),
-                "note": "algorithmic 4 S K flops per frame; the split path executes 4x that "
-                        "(hi/lo on both operands, Re and Im); peak = measured bf16 dense "
-                        "(FP16 same rate)"}
+                "note": f"algorithmic 4 S K flops per frame; the split path executes "
+                        f"{EXEC_FACTOR}x that (hi*hi, hi*lo and lo*hi products, Re and Im); "
+                        f"peak = measured bf16 dense (FP16 same rate)"}
 
     # classical path: frames once, then 8 B written + 8 B read per element per scan axis, and
     # the scan spectrum and the Wiener kernel read once by the detector pass

@@ -1,26 +1,45 @@
 // Phase accumulation on the 5th-generation tensor cores (tcgen05, TMEM), split FP16 precision:
 //   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. 14, Algorithm 2)
 //
-// Computed transposed, D^T = C^T E^T, so that every UMMA is as wide as the hardware allows:
-//   A operand (M = 128 rows): 64 coefficients, rows 0-63 their FP16 hi parts and rows 64-127 their
-//             lo parts, each column scaled by a power of two first (split_coeff_kernel);
-//   B operand (N = 256 rows): Re and Im of E for 128 scan frequencies, in FP16 hi and lo parts.
-// Two MMAs per 16-frame K-step (B = E_hi, then B = E_lo) accumulate in FP32 TMEM all four products
-// (c_hi + c_lo)(E_hi + E_lo) = c E up to FP16-split rounding (~2^-22 relative); the epilogue adds
-// the hi and lo rows and divides the scale out.
+// One CTA owns 128 scan frequencies (the MMA's M = 128 rows, one TMEM lane each) and 64
+// coefficients, and runs every staged frame of a flush through them:
+//   A operand (TMEM, M = 128 x K = 16 frames): the phase factors, generated in the kernel and
+//             written straight into tensor memory (tcgen05.st) in four FP16 parts, Re_hi,
+//             Re_lo, Im_hi and Im_lo, so they never pass through shared memory;
+//   B operand (SMEM, N = 128 rows): the 64 coefficients' FP16 hi parts (rows 0-63) and lo parts
+//             (rows 64-127), each column scaled by a power of two first (split_coeff_kernel),
+//             streamed in by 1-D TMA bulk copies.
+// Per 16-frame K-step four MMAs accumulate, in FP32 TMEM,
+//   D_re[v, 0:128] += Re_hi [c_hi | c_lo],   D_re[v, 0:64] += Re_lo c_hi,
+//   D_im[v, 0:128] += Im_hi [c_hi | c_lo],   D_im[v, 0:64] += Im_lo c_hi,
+// i.e. (E_hi + E_lo)(c_hi + c_lo) without the lo*lo product, which lies below FP32 rounding
+// (~2^-24 relative): the split carries about 22 significant bits.  The epilogue adds columns
+// k and 64 + k and divides the scale out.
 //
-// Kernel structure (one CTA per 128 scan frequencies x 64 or 128 coefficients):
-//   warps 0-7  build the B operand (Re/Im, hi/lo of E) for their rows in shared memory, in the
-//              no-swizzle K-major core-matrix layout, from the exact integer phase index and an
-//              FP64-built table; they then run the epilogue (tcgen05.ld -> shared-memory tiles ->
-//              coalesced H += (hi + lo) / scale).
-//   warp 8     streams the A operand (split coefficients, pre-arranged in the same layout) into
-//              shared memory with 1-D TMA bulk copies, in a pipeline of its own that runs up to
-//              8 stages ahead, hiding the copy latency.
-//   warp 9     allocates TMEM and one elected lane issues tcgen05.mma; tcgen05.commit frees
-//              each pipeline stage and finally signals the epilogue.
-// Every mbarrier wait is bounded; a wait that runs out records an error code in *status and the
-// CTA leaves the pipeline (after a bounded wait for its issued MMAs) and frees its TMEM.
+// Phase factors: E[v, s] = exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x)) (the 2-D scan DFT of
+// Eq. 14, separable in the scan axes).  For the 16 frames of a K-step that are consecutive
+// positions of one scan row (raster order), E[v, s0 + j] = E[v, s0] w_v^j with
+// w_v = exp(-2 pi i v_x / S_x): one FP32 table entry (exact integer index
+// m = (v_y s_y mod S_y)(lcm / S_y) + (v_x s_x mod S_x)(lcm / S_x) mod lcm into a table built in
+// FP64) times the powers w_v^j that each thread holds in registers, read once from the same
+// table.  Any other 16 frames take one table entry each.  Both are products of correctly rounded
+// FP32 values, within a few 2^-24 of the FP64 phase factor before the FP16 split.
+//
+// Accuracy bookkeeping: TMEM accumulates `seg_stages` stages (accum_segment frames); then the
+// epilogue adds the segment into H in FP32 and the next segment starts a fresh accumulator (the
+// tensor cores' FP32 accumulation error grows with the number of products added into one
+// accumulator).  All segments of a flush run in one launch.
+//
+// Warp roles (320 threads, one CTA per SM: all 512 TMEM columns):
+//   warps 0-7  E producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 (its scan frequencies) for
+//              K-step w / 4 of every stage; between segments they run the epilogue
+//              (tcgen05.ld -> shared-memory tile -> coalesced H += (hi + lo) / scale);
+//   warp 8     TMA loader of the B operand, up to SC stages ahead;
+//   warp 9     TMEM allocation; one elected lane issues tcgen05.mma and the commits.
+// TMEM columns: D_re 0-127, D_im 128-255, four A stages of 64 columns at 256-511
+// (stage st, K-step ks, part p: column 256 + 64 st + 32 ks + 8 p; two frames per column).
+// Every mbarrier wait is bounded; a wait that runs out records an error code in *status, the
+// CTA stops issuing work, waits (bounded) for the MMAs it issued and frees its TMEM.
 
 #include <cuda_fp16.h>
 
@@ -31,13 +50,17 @@ namespace wdd {
 
 namespace {
 
-constexpr int kTileV = 128;        // scan frequencies per CTA (Re and Im rows: UMMA N = 256)
+constexpr int kTileV = 128;        // scan frequencies per CTA (MMA M, TMEM lanes)
+constexpr int kTileK = 64;         // coefficients per CTA (B rows: 64 hi + 64 lo)
 constexpr int kChunk = 32;         // frames per pipeline stage (two UMMA K-steps of 16)
 constexpr int kProducers = 256;    // warps 0-7
 constexpr int kThreadsTC = 320;    // + TMA warp + MMA warp
-constexpr int kEKStepBytes = 2 * kTileV * 16 * 2;   // one K-step of an E operand: 256 rows x 16 frames
-constexpr int kEStageBytes = 2 * 2 * kEKStepBytes;  // hi and lo, two K-steps: 32 KB
-constexpr int kCMTileKStep = 128 * 16 * 2;          // one K-step of a 128-row coefficient tile: 4 KB
+constexpr int kStagesA = 4;        // A stages in TMEM
+constexpr int kColsD = 256;        // D_re + D_im
+constexpr int kTmemCols = 512;
+constexpr int kCKStepBytes = 128 * 16 * 2;          // one K-step of the B tile: 128 rows x 16 frames
+constexpr int kCStageBytes = 2 * kCKStepBytes;      // 8 KB per 32-frame stage
+constexpr int kTileStride = kTileK * 8 + 16;        // epilogue tile row: 64 float2 + 16 B pad
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
 // LBO = byte distance between the two core matrices along K, SBO = between 8-row groups.
@@ -58,13 +81,14 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                        uint32_t accumulate) {
+// D[tmem_d] (+)= A[tmem_a] * B[desc_b]: A from tensor memory, B from shared memory.
+__device__ __forceinline__ void mma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db,
+                                           uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -74,18 +98,56 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
-    uint32_t r[16];
+// Four 16-column TMEM loads of this thread's lane (addresses t0..t3) and the wait for them, in one
+// statement, so no use of the destination registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
+                                            float (&o0)[16], float (&o1)[16], float (&o2)[16],
+                                            float (&o3)[16]) {
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+        "%28,%29,%30,%31}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
+        "%44,%45,%46,%47}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,"
+        "%60,%61,%62,%63}, [%67];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
+          "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
+          "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
+          "=r"(r[62]), "=r"(r[63])
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) {
+        o0[i] = __uint_as_float(r[i]);
+        o1[i] = __uint_as_float(r[16 + i]);
+        o2[i] = __uint_as_float(r[32 + i]);
+        o3[i] = __uint_as_float(r[48 + i]);
+    }
+}
+
+// 32 consecutive TMEM columns of this thread's lane <- r[0..31], and the wait for the store.
+__device__ __forceinline__ void tmem_st32_wait(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
 }
 
 // x mod d for x < 2^32 with a precomputed 64-bit reciprocal (Lemire's fast modulo).
@@ -102,39 +164,54 @@ __device__ __forceinline__ uint32_t fastdiv(uint32_t x, FastMod f) {
     return (f.d == 1u) ? x : (uint32_t)__umul64hi(f.M, (uint64_t)x);
 }
 
+// Phase index m = (v_y s_y mod S_y) my + (v_x s_x mod S_x) mx mod lcm of scan position s (any
+// 32-bit value: the reductions keep m below lcm even for positions outside the scan).
+__device__ __forceinline__ uint32_t phase_index(uint32_t s, uint32_t vy, uint32_t vx, FastMod fy,
+                                                FastMod fx, uint32_t Sx, uint32_t my, uint32_t mx,
+                                                uint32_t lcm) {
+    const uint32_t sy = fastdiv(s, fx);
+    const uint32_t sx = s - sy * Sx;
+    uint32_t m = fastmod(vy * sy, fy) * my + fastmod(vx * sx, fx) * mx;
+    return m >= lcm ? m - lcm : m;
+}
+
+// hi and lo FP16 parts of two FP32 values, packed (first value in the low half).
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 struct TcArgs {
-    const uint16_t* csplit;   // pre-arranged A operand (see split_coeff_kernel)
+    const uint16_t* csplit;   // B operand (see split_coeff_kernel), [k-tile][stage][8 KB]
     const float* scale_inv;   // [Kp] 1 / column scale
     unsigned* colmax;         // [K] per-column max |c| (reset here for the next flush)
-    const int32_t* idx;       // [n] scan index of each staged frame
-    const uint2* tw16;        // [lcm] (re_hi | re_lo << 16, im_hi | im_lo << 16)
+    const int32_t* idx;       // [n_pad] scan index of each staged frame
+    const float2* tw;         // [lcm] exp(-2 pi i m / lcm), FP32 from FP64
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
-    int n_pad, S, K, NT, Sy, Sx, lcm, my, mx, stages_total, tmem_cols, tab_mode;
-    int stagesE, stagesC;     // pipeline depths (E: generated phase factors, C: coefficients)
-    int rotate;               // 1: each CTA starts at its own stage (see below)
-    int ktile_stages;         // stages per coefficient k-tile in the split operand
-    int last;                 // 1: the last launch of a flush (resets the column maxima)
+    int S, K, Sy, Sx, lcm, my, mx;
+    int stages_total;         // 32-frame stages of the flush
+    int seg_stages;           // stages per TMEM accumulation segment
+    int stagesC;              // B pipeline depth
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
 
-// Shared-memory layout of accumulate_tc_kernel (offsets from a 1024-byte aligned base).
+// Shared-memory layout (offsets from a 1024-byte aligned base).
 struct TcLayout {
-    size_t e, c, bar, tmem, scale, tab, total;
+    size_t c, tile, bar, tmem, scale, total;
 };
-__host__ __device__ inline TcLayout tc_layout(int NT, int stagesE, int stagesC, int lcm, int tab) {
+__host__ __device__ inline TcLayout tc_layout(int stagesC) {
     TcLayout L;
-    const size_t cStage = (size_t)(NT / 64) * 2 * kCMTileKStep;
-    L.e = 0;
-    L.c = L.e + (size_t)stagesE * kEStageBytes;
-    L.bar = L.c + (size_t)stagesC * cStage;
-    L.tmem = L.bar + 8 * (size_t)(2 * stagesE + 2 * stagesC + 1);
+    L.c = 0;
+    L.tile = L.c + (size_t)stagesC * kCStageBytes;
+    L.bar = L.tile + (size_t)kTileV * kTileStride;
+    L.tmem = L.bar + 8 * (size_t)(2 * kStagesA + 2 * stagesC + 3);
     L.scale = (L.tmem + 16 + 15) & ~size_t(15);
-    L.tab = (L.scale + 4 * (size_t)NT + 15) & ~size_t(15);
-    // tab: 0 none (global), 1 the table twice over (index m + d < 2 lcm), 2 that doubled table
-    // in 16 interleaved copies, one per bank pair
-    L.total = L.tab + (tab == 1 ? 16 * (size_t)lcm : tab == 2 ? 256 * (size_t)lcm : 0);
+    L.total = L.scale + 4 * (size_t)kTileK;
     return L;
 }
 
@@ -143,209 +220,235 @@ __device__ __forceinline__ void epilogue_barrier() {
     asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
-// 64-bit load from a shared-memory byte address.
-__device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
-    return v;
-}
-
-// kTab > 0: the phase table sits in shared memory twice over (entries m and m + lcm equal), so
-// the fast path adds a frame's phase step to a byte address with no reduction mod lcm; with
-// kTab == 2 the doubled table is stored in 16 interleaved copies (entry e, copy c at 8 (16 e + c)
-// bytes) and lane l reads copy l % 16, so the 16 lanes of a half-warp always hit 16 different
-// bank pairs, whatever entries they look up.  kTab == 0: the table is read from global memory
-// with reduced indices.
-template <int kTab>
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NT = a.NT;                 // coefficients per CTA (64 or 128)
-    const int MT = NT / 64;              // 128-row coefficient tiles (hi rows 0-63, lo rows 64-127)
-    const int SE = a.stagesE, SC = a.stagesC;
-    constexpr bool kTabSmem = kTab > 0;
-    constexpr uint32_t kEntryBytes = kTab == 2 ? 128u : 8u;   // stride of the table index
-    const TcLayout L = tc_layout(NT, SE, SC, a.lcm, kTab);
-    const int cStageBytes = MT * 2 * kCMTileKStep;
-    uint8_t* e_base = base + L.e;
+    const int SC = a.stagesC;
+    const TcLayout L = tc_layout(SC);
     uint8_t* c_base = base + L.c;
-    uint64_t* fullE = reinterpret_cast<uint64_t*>(base + L.bar);
-    uint64_t* emptyE = fullE + SE;
-    uint64_t* fullC = emptyE + SE;
+    uint8_t* tile = base + L.tile;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(base + L.bar);
+    uint64_t* emptyA = fullA + kStagesA;
+    uint64_t* fullC = emptyA + kStagesA;
     uint64_t* emptyC = fullC + SC;
-    uint64_t* done = emptyC + SC;
+    uint64_t* dfull = emptyC + SC;     // a segment's MMAs have completed (MMA warp -> epilogue)
+    uint64_t* dfree = dfull + 1;       // the epilogue has read D (epilogue -> MMA warp)
+    uint64_t* fin = dfree + 1;         // every issued MMA has completed (teardown)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
     float* s_scale = reinterpret_cast<float*>(base + L.scale);
-    uint2* s_tab = reinterpret_cast<uint2*>(base + L.tab);
-    const uint2* gtab = a.tw16;
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int v0 = blockIdx.x * kTileV;
-    const int k0 = blockIdx.y * NT;
-    // The CTAs of a launch walk the staged frames from evenly spread starting stages, so that at
-    // any moment they read different parts of the coefficient operand instead of all fetching the
-    // same lines from L2.  Only the order of the frames' FP32 additions changes.
+    const int k0 = blockIdx.y * kTileK;
     const int T = a.stages_total;
-    const int rot = a.rotate ? (int)(((long long)blockIdx.x * T) / gridDim.x) : 0;
-    auto stage_of = [T, rot](int it) { const int x = it + rot; return x >= T ? x - T : x; };
+    const int G = (T + a.seg_stages - 1) / a.seg_stages;   // segments
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < SE; ++s) {
-            mbar_init(&fullE[s], kProducers / 32);   // one arrival per producer warp
-            mbar_init(&emptyE[s], 1);
+        for (int s = 0; s < kStagesA; ++s) {
+            mbar_init(&fullA[s], kProducers / 32);   // one arrival per producer warp
+            mbar_init(&emptyA[s], 1);
         }
         for (int s = 0; s < SC; ++s) {
             mbar_init(&fullC[s], 1);
             mbar_init(&emptyC[s], 1);
         }
-        mbar_init(done, 1);
+        mbar_init(dfull, 1);
+        mbar_init(dfree, kProducers / 32);
+        mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (kTab == 1)
-        for (int t = threadIdx.x; t < 2 * a.lcm; t += blockDim.x)
-            s_tab[t] = a.tw16[t < a.lcm ? t : t - a.lcm];
-    if (kTab == 2)
-        for (int t = threadIdx.x; t < 32 * a.lcm; t += blockDim.x) {
-            const int e = t >> 4;
-            s_tab[t] = a.tw16[e < a.lcm ? e : e - a.lcm];
-        }
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(a.tmem_cols));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // The next launch may start now (it holds tensor memory only where this grid does not): a
-    // following segment runs its main loop, and a following projection its loads and MMAs,
-    // on SMs this grid leaves free; both wait (griddepcontrol.wait) before touching anything
-    // this grid writes.
+    // The next launch may start now (this CTA holds its tensor memory): it waits
+    // (griddepcontrol.wait) before touching anything this grid writes.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp < 8) {
-        // ---------------- E producers: phase factors as the B operand (N rows = Re, Im) ----
-        const int row = threadIdx.x & (kTileV - 1);    // 0..127
-        const int kstep = threadIdx.x >> 7;            // 0..1: which 16-frame K-step of a stage
-        // Rows of scan frequencies beyond S (last tile) are generated for v = 0; the epilogue
-        // never writes their results.
+        // ---------------- E producers, and the epilogue between segments ------------------
+        const int quarter = warp & 3;
+        const int ks = warp >> 2;                       // K-step of each stage this warp fills
+        const int row = quarter * 32 + lane;            // TMEM lane = frequency in the tile
+        // Rows beyond S (last tile) generate v = 0; the epilogue never writes them.
         const int v = (v0 + row < a.S) ? v0 + row : 0;
         const uint32_t vy = (uint32_t)(v / a.Sx);
         const uint32_t vx = (uint32_t)(v % a.Sx);
-        const int g_re = row >> 3, g_im = 16 + (row >> 3), r = row & 7;
-        // phase steps j * vx * mx mod lcm between a frame and its j-th successor in a scan row
-        // (as byte offsets into the shared table when it is there)
-        uint32_t dxj[16];
+        const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
+        const uint32_t lcm = (uint32_t)a.lcm;
+        // w_v^j = exp(-2 pi i j vx / Sx), j = 0..15, from the table (index j vx mx mod lcm)
+        float2 w[16];
         {
-            const uint32_t dx = vx * (uint32_t)a.mx;   // < lcm
+            const uint32_t d = vx * mx;   // < lcm
             uint32_t acc = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                dxj[j] = kTabSmem ? acc * kEntryBytes : acc;
-                acc += dx;
-                if (acc >= (uint32_t)a.lcm) acc -= (uint32_t)a.lcm;
+                w[j] = __ldg(a.tw + acc);
+                acc += d;
+                if (acc >= lcm) acc -= lcm;
             }
         }
-        const uint32_t tab_s = smem_u32(s_tab) + (kTab == 2 ? (uint32_t)(lane & 15) * 8u : 0u);
-        // first and last frame index of this thread's K-step, prefetched one stage ahead
-        const int32_t* ip0 = a.idx + (size_t)stage_of(0) * kChunk + kstep * 16;
+        const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16);
+        int ok = 1;   // warp-uniform: this warp has not given up
+        // first and last frame index of this warp's K-step, prefetched one stage ahead
+        const int32_t* ip0 = a.idx + ks * 16;
         int32_t nf = __ldg(ip0), nl = __ldg(ip0 + 15);
-        for (int it = 0; it < a.stages_total; ++it) {
-            const int st = it % SE;
-            const int32_t s_first = nf, s_last = nl;
-            if (it + 1 < a.stages_total) {
-                const int32_t* ipn = a.idx + (size_t)stage_of(it + 1) * kChunk + kstep * 16;
-                nf = __ldg(ipn);
-                nl = __ldg(ipn + 15);
-            }
-            // one lane per warp waits for the stage to be free and tells its warp
-            int ok = 1;
-            if (lane == 0) {
-                if (it >= SE && !mbar_wait(&emptyE[st], ((it / SE) - 1) & 1, a.wait_ns)) {
-                    atomicExch(a.status, 1u);
-                    s_abort = 1;
+        int it = 0;
+        for (int g = 0; g < G; ++g) {
+            const int it_end = (g + 1) * a.seg_stages < T ? (g + 1) * a.seg_stages : T;
+            for (; it < it_end; ++it) {
+                const int st = it % kStagesA;
+                const int32_t s_first = nf, s_last = nl;
+                if (it + 1 < T) {
+                    const int32_t* ipn = a.idx + (size_t)(it + 1) * kChunk + ks * 16;
+                    nf = __ldg(ipn);
+                    nl = __ldg(ipn + 15);
                 }
-                ok = !s_abort;
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            // Phase index of this thread's 16 frames, m = (vy sy mod Sy) my + (vx sx mod Sx) mx
-            // (mod lcm).  Fast path, decided per K-step (warp-uniform): the 16 frames are
-            // consecutive positions of one scan row, so m advances by dx = vx mx per frame.
-            // Otherwise each frame's index is decoded on its own.
-            const int32_t* ip = a.idx + (size_t)stage_of(it) * kChunk + kstep * 16;
-            uint32_t mm[16];   // table byte addresses (shared table) or reduced indices (global)
-            {
+                if (ok) {
+                    int good = 1;
+                    if (lane == 0) {
+                        if (it >= kStagesA &&
+                            !mbar_wait(&emptyA[st], ((it / kStagesA) - 1) & 1, a.wait_ns)) {
+                            atomicExch(a.status, 1u);
+                            s_abort = 1;
+                        }
+                        good = !s_abort;
+                    }
+                    ok = __shfl_sync(0xffffffffu, good, 0);
+                }
+                if (!ok) continue;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float2 e[16];
                 const uint32_t s0 = (uint32_t)s_first;
                 const uint32_t sy0 = fastdiv(s0, a.mod_x);
-                const uint32_t sx0 = s0 - sy0 * (uint32_t)a.Sx;
-                if (s_last == s_first + 15 && sx0 + 15u < (uint32_t)a.Sx) {
-                    uint32_t m = fastmod(vy * sy0, a.mod_y) * (uint32_t)a.my +
-                                 fastmod(vx * sx0, a.mod_x) * (uint32_t)a.mx;
-                    if (m >= (uint32_t)a.lcm) m -= (uint32_t)a.lcm;
-                    if (kTabSmem) {
-                        const uint32_t b = tab_s + m * kEntryBytes;
+                const uint32_t sx0 = s0 - sy0 * Sx;
+                if (s_last == s_first + 15 && sx0 + 15u < Sx) {
+                    // 16 consecutive positions of one scan row: E[v, s0] w^j
+                    const uint32_t m0 = phase_index(s0, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
+                    const float2 b = __ldg(a.tw + m0);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) mm[j] = b + dxj[j];   // entry m + d < 2 lcm
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const uint32_t mj = m + dxj[j];
-                            mm[j] = (mj >= (uint32_t)a.lcm) ? mj - (uint32_t)a.lcm : mj;
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        e[j] = make_float2(fmaf(b.x, w[j].x, -b.y * w[j].y),
+                                           fmaf(b.x, w[j].y, b.y * w[j].x));
                 } else {
+                    const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const uint32_t s = (uint32_t)__ldg(ip + j);
-                        const uint32_t sy = fastdiv(s, a.mod_x);
-                        const uint32_t sx = s - sy * (uint32_t)a.Sx;
-                        uint32_t m = fastmod(vy * sy, a.mod_y) * (uint32_t)a.my +
-                                     fastmod(vx * sx, a.mod_x) * (uint32_t)a.mx;
-                        m = (m >= (uint32_t)a.lcm) ? m - (uint32_t)a.lcm : m;
-                        mm[j] = kTabSmem ? tab_s + m * kEntryBytes : m;
+                        const uint32_t m = phase_index((uint32_t)__ldg(ip + j), vy, vx, a.mod_y,
+                                                       a.mod_x, Sx, my, mx, lcm);
+                        e[j] = __ldg(a.tw + m);
+                    }
+                }
+                uint32_t r[32];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 8 columns of frame pairs each
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    split2(e[2 * c].x, e[2 * c + 1].x, r[c], r[8 + c]);
+                    split2(e[2 * c].y, e[2 * c + 1].y, r[16 + c], r[24 + c]);
+                }
+                tmem_st32_wait(t_lane + (uint32_t)(kColsD + st * 64 + ks * 32), r);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullA[st]);
+            }
+            // ---------------- epilogue of segment g: H[v, k] += (D[k] + D[64 + k]) / scale ----
+            // The scales come from the split pre-pass and H from the previous flush: wait for
+            // the launch before this one (a no-op after the first time).
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            if (g == 0)
+                for (int t = threadIdx.x; t < kTileK; t += kProducers) {
+                    const int k = k0 + t;
+                    s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+                }
+            int go = 0;
+            if (ok) {
+                int good = 1;
+                if (lane == 0) {
+                    good = mbar_wait(dfull, g & 1, a.wait_ns) ? 1 : 0;
+                    if (!good) {
+                        atomicExch(a.status, 4u);
+                        s_abort = 1;
+                    }
+                    good = good && !s_abort;
+                }
+                go = __shfl_sync(0xffffffffu, good, 0);
+                ok = go;
+            }
+            epilogue_barrier();   // s_scale written; the tile is free
+            const int half = warp >> 2;
+            if (go) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float2* trow = reinterpret_cast<float2*>(tile + (size_t)row * kTileStride);
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c0 = half * 32 + cc * 16;   // coefficient column within the tile
+                    float rh[16], rl[16], ih[16], il[16];
+                    tmem_ld16x4(t_lane + (uint32_t)c0, t_lane + (uint32_t)(64 + c0),
+                                t_lane + (uint32_t)(128 + c0), t_lane + (uint32_t)(192 + c0),
+                                rh, rl, ih, il);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float s0v = s_scale[c0 + i], s1v = s_scale[c0 + i + 1];
+                        *reinterpret_cast<float4*>(trow + c0 + i) =
+                            make_float4((rh[i] + rl[i]) * s0v, (ih[i] + il[i]) * s0v,
+                                        (rh[i + 1] + rl[i + 1]) * s1v, (ih[i + 1] + il[i + 1]) * s1v);
+                    }
+                }
+                // D has been read: the next segment's MMAs may overwrite it
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(dfree);
+            }
+            epilogue_barrier();   // the tile is complete
+            if (go) {
+                // warp w updates tile rows w, w + 8, ...; lane l the coefficients l and l + 32
+                for (int vb = 0; vb < kTileV / 8; vb += 4) {
+                    float2 hv[4][2];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int vv = v0 + warp + 8 * (vb + i);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int k = k0 + hh * 32 + lane;
+                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                                                              : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int vr = warp + 8 * (vb + i);
+                        const int vv = v0 + vr;
+                        const float2* trow = reinterpret_cast<const float2*>(tile + (size_t)vr * kTileStride);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int kl = hh * 32 + lane;
+                            const int k = k0 + kl;
+                            if (vv < a.S && k < a.K) {
+                                const float2 x = trow[kl];
+                                a.H[(size_t)vv * a.K + k] =
+                                    make_float2(hv[i][hh].x + x.x, hv[i][hh].y + x.y);
+                            }
+                        }
                     }
                 }
             }
-            uint8_t* ehi = e_base + (size_t)st * kEStageBytes + kstep * kEKStepBytes;
-            uint8_t* elo = ehi + 2 * kEKStepBytes;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                uint2 q[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) q[e] = kTabSmem ? lds_u2(mm[c * 8 + e]) : gtab[mm[c * 8 + e]];
-                uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    rh[e] = __byte_perm(q[2 * e].x, q[2 * e + 1].x, 0x5410);
-                    rl[e] = __byte_perm(q[2 * e].x, q[2 * e + 1].x, 0x7632);
-                    ih[e] = __byte_perm(q[2 * e].y, q[2 * e + 1].y, 0x5410);
-                    il[e] = __byte_perm(q[2 * e].y, q[2 * e + 1].y, 0x7632);
-                }
-                const int o_re = g_re * 256 + c * 128 + r * 16;
-                const int o_im = g_im * 256 + c * 128 + r * 16;
-                *reinterpret_cast<uint4*>(ehi + o_re) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                *reinterpret_cast<uint4*>(ehi + o_im) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                *reinterpret_cast<uint4*>(elo + o_re) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                *reinterpret_cast<uint4*>(elo + o_im) = make_uint4(il[0], il[1], il[2], il[3]);
-            }
-            fence_async_smem();    // this thread's stores -> visible to the tensor core
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&fullE[st]);
         }
     } else if (warp == 8) {
-        // ---------------- C loader (TMA), running up to SC stages ahead ----------------
+        // ---------------- B loader (TMA), running up to SC stages ahead ----------------
         if (lane == 0) {
             // the split coefficients come from the launch before (the split pre-pass)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
-                                 (size_t)blockIdx.y * a.ktile_stages * cStageBytes;
-            for (int it = 0; it < a.stages_total; ++it) {
+                                 (size_t)blockIdx.y * T * kCStageBytes;
+            for (int it = 0; it < T; ++it) {
                 const int sc = it % SC;
                 if (it >= SC && !mbar_wait(&emptyC[sc], ((it / SC) - 1) & 1, a.wait_ns)) {
                     atomicExch(a.status, 2u);
@@ -353,167 +456,83 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     break;
                 }
                 if (s_abort) break;
-                mbar_arrive_tx(&fullC[sc], cStageBytes);
-                tma_load_1d(c_base + (size_t)sc * cStageBytes, src + (size_t)stage_of(it) * cStageBytes,
-                            cStageBytes, &fullC[sc]);
+                mbar_arrive_tx(&fullC[sc], kCStageBytes);
+                tma_load_1d(c_base + (size_t)sc * kCStageBytes, src + (size_t)it * kCStageBytes,
+                            kCStageBytes, &fullC[sc]);
             }
         }
     } else {
-        // ---------------- MMA issuer: D_j[coefficient row][Re v | Im v] --------------------
-        // With one coefficient tile the E_hi and E_lo products go to two accumulators (added in
-        // the epilogue), so consecutive MMAs do not wait on each other's accumulation.
-        // Descriptors are formed once and advanced by the byte offsets of stages and K-steps.
+        // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = instr_desc(128, 2 * kTileV);
-            const uint64_t de0 = smem_desc(smem_u32(e_base), 128, 256);
+            const uint32_t id_full = instr_desc(128, 2 * kTileK);   // B = [c_hi | c_lo]
+            const uint32_t id_hi = instr_desc(128, kTileK);         // B = c_hi
             const uint64_t dc0 = smem_desc(smem_u32(c_base), 128, 256);
-            const int nacc = MT == 1 ? 2 : 1;
-            uint32_t acc = 0;
-            int st = 0, sc = 0;
-            uint32_t pe = 0, pc = 0;
-            for (int it = 0; it < a.stages_total; ++it) {
-                if (!mbar_wait(&fullC[sc], pc, a.wait_ns) || !mbar_wait(&fullE[st], pe, a.wait_ns)) {
+            const uint32_t d_re = tmem, d_im = tmem + 128u;
+            int sc = 0;
+            uint32_t pa = 0, pc = 0;
+            int st = 0;
+            bool run = true;
+            for (int it = 0; it < T && run; ++it) {
+                const bool seg_start = (it % a.seg_stages) == 0;
+                if (seg_start && it > 0) {
+                    // the epilogue must have read the previous segment out of D
+                    if (!mbar_wait(dfree, ((it / a.seg_stages) - 1) & 1, a.wait_ns)) {
+                        atomicExch(a.status, 5u);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+                if (!mbar_wait(&fullC[sc], pc, a.wait_ns) || !mbar_wait(&fullA[st], pa, a.wait_ns)) {
                     atomicExch(a.status, 3u);
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t de = de0 + (uint64_t)((st * kEStageBytes) >> 4);
-                const uint64_t dc = dc0 + (uint64_t)((sc * cStageBytes) >> 4);
+                const uint64_t dc = dc0 + (uint64_t)((sc * kCStageBytes) >> 4);
+                const uint32_t ta = tmem + (uint32_t)(kColsD + st * 64);
 #pragma unroll
-                for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    const uint64_t e_h = de + (uint64_t)((ks * kEKStepBytes) >> 4);
-                    const uint64_t e_l = e_h + (uint64_t)((2 * kEKStepBytes) >> 4);
-                    for (int j = 0; j < MT; ++j) {
-                        const uint64_t cd = dc + (uint64_t)(((j * 2 + ks) * kCMTileKStep) >> 4);
-                        const uint32_t d = tmem + (uint32_t)(j * nacc * 2 * kTileV);
-                        mma_f16(d, cd, e_h, idesc, acc);
-                        mma_f16(d + (uint32_t)((nacc - 1) * 2 * kTileV), cd, e_l, idesc,
-                                nacc == 2 ? acc : 1u);
-                    }
-                    acc = 1u;
+                for (int k2 = 0; k2 < kChunk / 16; ++k2) {
+                    const uint64_t db = dc + (uint64_t)((k2 * kCKStepBytes) >> 4);
+                    const uint32_t a0 = ta + (uint32_t)(k2 * 32);
+                    const uint32_t acc = (seg_start && k2 == 0) ? 0u : 1u;
+                    mma_f16_ts(d_re, a0, db, id_full, acc);          // Re_hi [c_hi | c_lo]
+                    mma_f16_ts(d_re, a0 + 8u, db, id_hi, 1u);        // Re_lo c_hi
+                    mma_f16_ts(d_im, a0 + 16u, db, id_full, acc);    // Im_hi [c_hi | c_lo]
+                    mma_f16_ts(d_im, a0 + 24u, db, id_hi, 1u);       // Im_lo c_hi
                 }
-                mma_commit(&emptyE[st]);   // free both stages once these MMAs have read them
+                mma_commit(&emptyA[st]);   // free both stages once these MMAs have read them
                 mma_commit(&emptyC[sc]);
-                if (++st == SE) { st = 0; pe ^= 1u; }
+                if ((it + 1) % a.seg_stages == 0 || it + 1 == T) mma_commit(dfull);
+                if (++st == kStagesA) { st = 0; pa ^= 1u; }
                 if (++sc == SC) { sc = 0; pc ^= 1u; }
             }
-            mma_commit(done);              // all issued MMAs complete -> epilogue
+            // teardown: every MMA issued above completes before TMEM is freed
+            mma_commit(fin);
+            if (!mbar_wait(fin, 0, a.wait_ns)) atomicExch(a.status, 6u);
         }
     }
 
-    // H (and the column maxima) may still be written by the previous launch: wait for it to
-    // complete before the epilogue reads them.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    // ---------------- epilogue: warps 0-7 ----------------
-    // TMEM lane = coefficient row (0-63: hi part, 64-127: lo part); column = Re v | Im v.
-    // Warps whose lane quarter holds hi rows write tile T_hi[v][k], the others T_lo[v][k]
-    // (both in the freed E stage buffers), then all eight warps add T_hi + T_lo, scale and
-    // update H with whole 128-byte row segments.
-    if (warp < 8) {
-        int ok = 1;
-        if (lane == 0) {
-            ok = mbar_wait(done, 0, a.wait_ns) ? 1 : 0;
-            if (!ok) atomicExch(a.status, 4u);
-            ok = ok && !s_abort;
-        }
-        const bool go = __shfl_sync(0xffffffffu, ok, 0) != 0;   // tcgen05.ld needs the whole warp
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // column scales (from the split pre-pass; read after the wait above, ordered before
-        // their use by the epilogue barrier below)
-        for (int t = threadIdx.x; t < NT; t += kProducers) {
-            const int k = k0 + t;
-            s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
-        }
-        const int quarter = warp & 3;                 // TMEM lanes 32 q .. 32 q + 31
-        const int half = warp >> 2;                   // which half of the v columns
-        const int krow = (quarter & 1) * 32 + lane;   // coefficient within the m-tile
-        float2* T = reinterpret_cast<float2*>(e_base) + (size_t)(quarter >> 1) * kTileV * 64;
-        const int nacc = MT == 1 ? 2 : 1;
-        for (int j = 0; j < MT; ++j) {
-            if (go) {
-                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                           (uint32_t)(j * nacc * 2 * kTileV);
-                for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
-                    float re[16], im[16];
-                    tmem_ld16(lane_addr + (uint32_t)c0, re);
-                    tmem_ld16(lane_addr + (uint32_t)(kTileV + c0), im);
-                    if (nacc == 2) {   // E_lo products in the second accumulator
-                        float re2[16], im2[16];
-                        tmem_ld16(lane_addr + (uint32_t)(2 * kTileV + c0), re2);
-                        tmem_ld16(lane_addr + (uint32_t)(3 * kTileV + c0), im2);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            re[i] += re2[i];
-                            im[i] += im2[i];
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) T[(size_t)(c0 + i) * 64 + krow] = make_float2(re[i], im[i]);
-                }
-            }
-            epilogue_barrier();
-            if (go) {
-                // Each warp updates rows vr = warp + 8 i of the tile, a lane two coefficients
-                // per row; the H values of 8 rows are loaded before any is stored, so the loads
-                // overlap instead of waiting on each other's stores.
-                const float2* Thi = reinterpret_cast<const float2*>(e_base);
-                const float2* Tlo = Thi + (size_t)kTileV * 64;
-                for (int vb = 0; vb < kTileV / 8; vb += 8) {
-                    float2 hv[8][2];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int vv = v0 + warp + 8 * (vb + i);
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int k = k0 + j * 64 + hh * 32 + lane;
-                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
-                                                              : make_float2(0.f, 0.f);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int vr = warp + 8 * (vb + i);
-                        const int vv = v0 + vr;
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int kl = hh * 32 + lane;
-                            const int k = k0 + j * 64 + kl;
-                            if (vv < a.S && k < a.K) {
-                                const float2 x = Thi[(size_t)vr * 64 + kl], y = Tlo[(size_t)vr * 64 + kl];
-                                const float sc = s_scale[j * 64 + kl];
-                                float2 h = hv[i][hh];
-                                h.x = fmaf(x.x + y.x, sc, h.x);
-                                h.y = fmaf(x.y + y.y, sc, h.y);
-                                a.H[(size_t)vv * a.K + k] = h;
-                            }
-                        }
-                    }
-                }
-            }
-            epilogue_barrier();
-        }
-    }
-    if (blockIdx.x == 0 && blockIdx.y == 0)
-        if (a.last)
-            for (int t = threadIdx.x; t < a.K; t += blockDim.x) a.colmax[t] = 0u;
+    // column maxima for the next flush: reset by the producer warps, which have passed
+    // griddepcontrol.wait, i.e. after the split pre-pass has read them
+    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < 8)
+        for (int t = threadIdx.x; t < a.K; t += kProducers) a.colmax[t] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 9) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(a.tmem_cols));
+                     "r"(kTmemCols));
     }
 }
 
 // Splits the staged FP32 coefficients into FP16 hi/lo parts with a power-of-two scale per column
-// and writes them as the A operand of accumulate_tc_kernel:
-//   [k-tile][stage][m-tile][K-step][row group][core matrix b/8 % 2][row % 8][b % 8]
-// where an m-tile holds 64 coefficients, rows 0-63 their hi parts and rows 64-127 their lo
-// parts.  Frames beyond n and coefficients beyond K are zero.  One thread per (frame, column).
+// and writes them as the B operand of accumulate_tc_kernel, K-major core matrices:
+//   [k-tile of 64][stage][K-step][row group][core matrix b/8 % 2][row % 8][b % 8]
+// where rows 0-63 of a k-tile hold its 64 coefficients' hi parts and rows 64-127 their lo parts.
+// Frames beyond n and coefficients beyond K are zero.  One thread per (frame, column).
 __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
-                                   int n, int n_pad, int K, int Kp, int NT) {
+                                   int n, int n_pad, int K, int Kp) {
     // the accumulation launched next sets up and generates phase factors meanwhile; it reads
     // this kernel's output only after griddepcontrol.wait.  Its producers read the staged scan
     // indices at once: that is safe because this kernel is launched without programmatic
@@ -532,15 +551,12 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
     const float x = (b < n && kk < K) ? c[(size_t)b * K + kk] * sc : 0.f;
     const __half hi = __float2half_rn(x);
     const __half lo = __float2half_rn(x - __half2float(hi));
-    const int ktile = kk / NT, kl = kk % NT;
-    const int mtile = kl / 64, km = kl % 64;
-    const int MT = NT / 64;
+    const int ktile = kk / kTileK, km = kk % kTileK;
     const int stage = b / kChunk, bs = b % kChunk;
     const int ks = bs / 16, bk = bs % 16;
     const int stages_total = n_pad / kChunk;
-    const size_t stage_halves = (size_t)MT * 2 * (kCMTileKStep / 2);
-    const size_t base = ((size_t)ktile * stages_total + stage) * stage_halves +
-                        (size_t)(mtile * 2 + ks) * (kCMTileKStep / 2);
+    const size_t base = ((size_t)ktile * stages_total + stage) * (kCStageBytes / 2) +
+                        (size_t)ks * (kCKStepBytes / 2);
     const int rh = km, rl = 64 + km;
     const size_t in_hi = (size_t)(rh >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rh & 7) * 8 + (bk & 7);
     const size_t in_lo = (size_t)(rl >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rl & 7) * 8 + (bk & 7);
@@ -573,62 +589,36 @@ cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cud
 bool split_path_available() { return true; }
 
 cudaError_t prepare_split_kernels() {
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<0>));
-    if (e == cudaSuccess)
-        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<1>));
-    if (e == cudaSuccess)
-        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<2>));
-    return e;
+    return allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel));
 }
 
-// Coefficients per CTA: 64 (one hi/lo m-tile) or 128 (two).
-int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
+// Coefficients per CTA.
+int split_tile_n(int /*K*/) { return kTileK; }
 
-// Pipeline depths for a tile width NT within the shared-memory budget.  The E region must hold
-// the two epilogue tiles (128 KB), so it keeps 4 stages; C takes what is left, up to 8, after
-// the phase table.  The table goes to shared memory in the best form that leaves 3 or more C
-// stages: the bank-interleaved copies, else the doubled table; otherwise it stays in global.
-static void split_stages(int NT, int lcm, int* se, int* sc, int* tab) {
+// B pipeline depth: as deep as the shared memory allows (up to 16 stages).  The kernel then needs
+// more shared memory than a projection CTA leaves, so no other CTA of a step shares its SM (each
+// would wait for tensor memory this CTA holds).
+static int split_stages_c() {
     const size_t limit = 226 * 1024 - 1024;   // dynamic bytes after the alignment slack
-    const int E = 4;
-    for (int mode = 2; mode >= 1; --mode)
-        for (int C = 8; C >= 3; --C)
-            if (tc_layout(NT, E, C, lcm, mode).total <= limit) {
-                *se = E;
-                *sc = C;
-                *tab = mode;
-                return;
-            }
-    int C = 8;
-    while (C > 2 && tc_layout(NT, E, C, lcm, 0).total > limit) --C;
-    *se = E;
-    *sc = C;
-    *tab = 0;
+    int C = 16;
+    while (C > 2 && tc_layout(C).total > limit) --C;
+    return C;
 }
 
-size_t split_smem_bytes(int NT) {
-    int E, C, T;
-    split_stages(NT, 1, &E, &C, &T);
-    return 1024 + tc_layout(NT, E, C, 1, 0).total;
-}
+size_t split_smem_bytes(int /*NT*/) { return 1024 + tc_layout(split_stages_c()).total; }
 
-// Kernel launches of one flush of n staged frames: the split pre-pass and one per segment.
-int split_launch_count(int n, int segment) {
-    const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
-    return 1 + (n_pad + segment - 1) / segment;
-}
+// Kernel launches of one flush: the split pre-pass and the accumulation.
+int split_launch_count(int /*n*/, int /*segment*/) { return 2; }
 
 size_t split_coeff_bytes(int K, int depth_pad) {
-    const int NT = split_tile_n(K);
-    const int Kp = (K + NT - 1) / NT * NT;
+    const int Kp = (K + kTileK - 1) / kTileK * kTileK;
     return (size_t)Kp * depth_pad * 2 * 2;   // hi and lo halves
 }
 
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const int NT = split_tile_n(P->K);
-    const int Kp = (P->K + NT - 1) / NT * NT;
+    const int Kp = (P->K + kTileK - 1) / kTileK * kTileK;
     const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
     if (n_pad > P->depth_pad) return cudaErrorInvalidValue;
     // 1. split the coefficients (per-column scale from the projection's running max)
@@ -636,72 +626,45 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
         const size_t total = (size_t)n_pad * Kp;
         split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
             c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, n, n_pad,
-            P->K, Kp, NT);
+            P->K, Kp);
     }
-    // 2. tensor-core accumulation
+    // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
     TcArgs a;
     a.csplit = reinterpret_cast<const uint16_t*>(P->d_bsplit);
     a.scale_inv = P->d_scale_inv;
     a.colmax = P->d_colmax;
     a.idx = idx;
-    a.tw16 = reinterpret_cast<const uint2*>(P->d_tw16);
+    a.tw = P->d_tw;
     a.H = P->d_H;
     a.status = P->d_status;
-    a.n_pad = n_pad;
     a.S = P->S;
     a.K = P->K;
-    a.NT = NT;
     a.Sx = P->Sx;
     a.Sy = P->Sy;
     a.lcm = P->lcm;
     a.my = P->lcm / P->Sy;
     a.mx = P->lcm / P->Sx;
     a.stages_total = n_pad / kChunk;
-    a.tmem_cols = 4 * kTileV;   // two 256-column accumulators (E_hi / E_lo parts, or two tiles)
+    a.seg_stages = P->segment / kChunk > 0 ? P->segment / kChunk : 1;
+    a.stagesC = split_stages_c();
     a.wait_ns = kDeviceWaitNs;
-    a.rotate = 1;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
-    split_stages(NT, P->lcm, &a.stagesE, &a.stagesC, &a.tab_mode);
-    const size_t smem = 1024 + tc_layout(NT, a.stagesE, a.stagesC, P->lcm, a.tab_mode).total;
-    dim3 grid((P->S + kTileV - 1) / kTileV, Kp / NT);
-    // One launch per segment of at most P->segment staged frames: the tensor cores' FP32
-    // accumulation loses a little precision with every MMA added into an accumulator (error
-    // linear in the number added), so long flushes run as several launches whose sums are added
-    // into H in FP32 in between.
-    const int stages_all = n_pad / kChunk;
-    const int seg = P->segment / kChunk;
-    const size_t c_stage_halves = (size_t)(NT / 64) * kCMTileKStep;   // one stage of one k-tile
-    a.ktile_stages = stages_all;
-    for (int s0 = 0; s0 < stages_all; s0 += seg) {
-        TcArgs b = a;
-        b.stages_total = stages_all - s0 < seg ? stages_all - s0 : seg;
-        b.csplit = a.csplit + (size_t)s0 * c_stage_halves;
-        b.idx = idx + (size_t)s0 * kChunk;
-        b.last = s0 + seg >= stages_all ? 1 : 0;
-        // every segment overlaps the launch before it (programmatic dependent launch): the first
-        // sets up and generates phase factors while the split pre-pass runs and loads the split
-        // coefficients after griddepcontrol.wait; later ones overlap the previous segment's
-        // tail and read H only after griddepcontrol.wait
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(kThreadsTC, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e;
-        if (b.tab_mode == 2)
-            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<2>, b);
-        else if (b.tab_mode == 1)
-            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<1>, b);
-        else
-            e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<0>, b);
-        if (e != cudaSuccess) return e;
-    }
+    // the launch overlaps the split pre-pass (programmatic dependent launch): it allocates
+    // tensor memory and generates phase factors meanwhile, and loads the split coefficients and
+    // scales, and touches H, only after griddepcontrol.wait
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((P->S + kTileV - 1) / kTileV, Kp / kTileK);
+    cfg.blockDim = dim3(kThreadsTC, 1, 1);
+    cfg.dynamicSmemBytes = 1024 + tc_layout(a.stagesC).total;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
