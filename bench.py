@@ -326,6 +326,103 @@ def run_serving(args) -> int:
 
 
 # ---------------------------------------------------------------------------------------------
+# extras on the default line: the accumulation at the serving ranks, and a slice of the serving mix
+# ---------------------------------------------------------------------------------------------
+
+RANKS = ((64, "hg_tensor"), (128, "hg_energy"), (256, "hg_tensor"))
+
+
+def accumulate_by_rank(acq, d_frames, idx, stream, peaks, n_frames=4096, reps=5) -> dict:
+    """The tensor-core accumulation of one flush of n_frames staged frames on this scan at ranks
+    K = 64, 128 and 256 (the serving mix's ranks): device time of the flush (split pre-pass and
+    accumulation launch, CUDA events around them on the launch stream), algorithmic 4 S K flops
+    per frame and the EXEC_FACTOR x that the split path executes, against the measured bf16
+    dense peak.  Median of `reps` flushes."""
+    from paper_2212_01309_gb300 import wdd
+    S = acq.scan_y * acq.scan_x
+    out = {}
+    for K, basis in RANKS:
+        p = wdd.params_from_acquisition(acq, basis=basis, rank_k=K, epsilon=1e-3,
+                                        precision="split", max_batch=1024,
+                                        accum_depth=n_frames, coalesce_frames=1024,
+                                        overlap_pushes=True)
+        ms = []
+        with wdd.Plan(p) as g:
+            for r in range(reps + 1):
+                g.reset(stream=stream)
+                for a in range(0, n_frames, 1024):
+                    g.push(d_frames[a:a + 1024], idx[a:a + 1024], stream=stream)
+                g.set_stage_timing(True)
+                g.flush(stream=stream)
+                g.set_stage_timing(False)
+                st = g.stage_times()
+                if r > 0:
+                    ms.append(st["accumulate"][0])
+            g.check_device()
+        flush_ms = float(np.median(ms))
+        alg = 4.0 * S * K * n_frames / (flush_ms * 1e-3) / 1e12
+        out[f"K{K}"] = {"basis": basis, "flush_frames": n_frames, "flush_ms": flush_ms,
+                        "achieved_algorithmic": alg, "achieved_executed": EXEC_FACTOR * alg,
+                        "peak": peaks["bf16"], "unit": "TFLOP/s",
+                        "frac_algorithmic": alg / peaks["bf16"],
+                        "frac_executed": EXEC_FACTOR * alg / peaks["bf16"]}
+    return out
+
+
+def serving_slice(seconds=2.0, deadline_s=0.02) -> dict:
+    """The serving mix (six sessions) over the first `seconds` of its seeded 20k frames/s
+    arrival schedule: open loop at the schedule with a snapshot deadline, closed loop (every
+    batch available at once) on the split path, and closed loop on the plain FP32 path; each
+    session ends (final snapshot) with the slice's last frame."""
+    import torch
+
+    import synth
+    from paper_2212_01309_gb300 import serving, wdd
+    from synth.generator import NOISE_BLOCK
+    from synth.torch_gen import TorchFrames
+    mix = synth.serving_mix()
+    arrivals = synth.serving_arrivals([a.n_frames for a, _ in mix])
+    arrivals = [a for a in arrivals if a[0] <= seconds]
+    need = [0] * len(mix)
+    for _, sid, start, count in arrivals:
+        need[sid] = max(need[sid], start + count)
+    specs = {"split": [], "fp32": []}
+    for sid, (acq, rc) in enumerate(mix):
+        if need[sid] == 0:
+            continue
+        gen = TorchFrames(acq)
+        nblk = (need[sid] + NOISE_BLOCK - 1) // NOISE_BLOCK
+        frames = torch.cat([gen.block(b) for b in range(nblk)])[:need[sid]].contiguous()
+        for prec in ("split", "fp32"):
+            kw = dict(precision="split", accum_depth=2048, coalesce_frames=1024,
+                      overlap_pushes=True) if prec == "split" else dict(precision="fp32",
+                                                                         accum_depth=0)
+            p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                            epsilon=rc["epsilon"], max_batch=512, **kw)
+            specs[prec].append(serving.Session(sid=sid, params=p, frames=frames,
+                                               n_frames=need[sid]))
+    torch.cuda.synchronize()
+    out = {"schedule_s": seconds, "frames": int(sum(need)), "arrival_rate_fps": 20000,
+           "snapshot_every": 1024, "deadline_ms": deadline_s * 1e3,
+           "sessions": sum(1 for n in need if n)}
+    runs = [("open_loop_deadline", "split", True, deadline_s),
+            ("closed_loop", "split", False, None),
+            ("closed_loop_fp32_plain", "fp32", False, None)]
+    for mode, prec, open_loop, delay in runs:
+        srv = serving.Server(snapshot_every=1024, use_graphs=True, snapshot_max_delay_s=delay)
+        for sp in specs[prec]:
+            srv.add_session(sp)
+        srv.admit_now()
+        torch.cuda.synchronize()
+        st = srv.run(arrivals, open_loop=open_loop, timeout_s=600)
+        out[mode] = {"frames_per_s": st["frames_per_s"], "p50_ms": st["latency_p50_ms"],
+                     "p99_ms": st["latency_p99_ms"], "wall_s": st["wall_s"]}
+    out["speedup_vs_fp32_plain"] = (out["closed_loop"]["frames_per_s"] /
+                                    out["closed_loop_fp32_plain"]["frames_per_s"])
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
 

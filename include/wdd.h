@@ -57,11 +57,11 @@ typedef enum { WDD_BASIS_FOURIER_FULL = 0, WDD_BASIS_HG_TENSOR = 1, WDD_BASIS_HG
 
 /* Arithmetic of the streaming steps.
  *  FP32   projection and phase accumulation in FP32 FMA on the SIMT cores.
- *  SPLIT  tensor cores: phase factors and coefficients split into hi + lo FP16 parts, all four
- *         products accumulated in FP32 (the lo*lo term lies below FP32 rounding); frames and the
- *         projection basis likewise on the tensor cores where the frame type and detector width
- *         allow (see wdd_plan_info.proj_tensor).  Staged frames are accumulated accum_depth at a
- *         time, in launches of accum_segment frames. */
+ *  SPLIT  tensor cores: phase factors and coefficients split into hi + lo FP16 parts, the
+ *         hi*hi, hi*lo and lo*hi products accumulated in FP32 (the lo*lo term lies below FP32
+ *         rounding); frames and the projection basis likewise on the tensor cores where the
+ *         frame type and detector width allow (see wdd_plan_info.proj_tensor).  Staged frames
+ *         are accumulated accum_depth at a time, in TMEM segments of accum_segment frames. */
 typedef enum { WDD_PREC_FP32 = 0, WDD_PREC_SPLIT = 1 } wdd_precision;
 
 /* How staged frames are added into the accumulator H.
@@ -108,11 +108,11 @@ typedef struct {
                                  a detector DMA or by copies.  Later chunks of one push always
                                  overlap (their predecessor is the push's own projection). */
     int32_t accum_segment;    /* SPLIT: staged frames summed in the tensor cores' FP32 accumulators
-                                 per launch (rounded up to a multiple of 32); the launches' sums
-                                 are added into H in FP32.  The accumulator error grows linearly
-                                 with the segment (relative 3.2e-7 at 256 frames, 7.6e-7 at 1024,
-                                 3.8e-6 at 4096 on a 128x128 scan); longer segments run faster.
-                                 0 = 1024. */
+                                 before they are added into H in FP32 (rounded up to a multiple
+                                 of 64; all segments of a flush run in one launch).  The
+                                 accumulator error grows linearly with the segment (relative
+                                 3.2e-7 at 256 frames, 7.6e-7 at 1024, 3.8e-6 at 4096 on a
+                                 128x128 scan); longer segments run slightly faster.  0 = 1024. */
     int32_t accum_mode;       /* wdd_accum_mode: how staged frames are added into H            */
     int32_t coalesce_frames;  /* tensor-core projection: device or pinned-host pushes are gathered
                                  until this many frames are pending (at most 1024, from at most 16

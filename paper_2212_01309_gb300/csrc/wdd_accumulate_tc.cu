@@ -30,14 +30,19 @@
 // tensor cores' FP32 accumulation error grows with the number of products added into one
 // accumulator).  All segments of a flush run in one launch.
 //
-// Warp roles (320 threads, one CTA per SM: all 512 TMEM columns):
-//   warps 0-7  E producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 (its scan frequencies) for
-//              K-step w / 4 of every stage; between segments they run the epilogue
-//              (tcgen05.ld -> shared-memory tile -> coalesced H += (hi + lo) / scale);
-//   warp 8     TMA loader of the B operand, up to SC stages ahead;
-//   warp 9     TMEM allocation; one elected lane issues tcgen05.mma and the commits.
-// TMEM columns: D_re 0-127, D_im 128-255, four A stages of 64 columns at 256-511
-// (stage st, K-step ks, part p: column 256 + 64 st + 32 ks + 8 p; two frames per column).
+// Warp roles (576 threads, one CTA per SM: all 512 TMEM columns):
+//   warps 0-15  E producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 (its scan frequencies) for
+//               K-step w / 4 of every 64-frame stage; between segments they run the epilogue
+//               (tcgen05.ld -> shared-memory tile -> coalesced H += (hi + lo) / scale);
+//   warp 16     TMA loader of the B operand;
+//   warp 17     TMEM allocation; one elected lane issues tcgen05.mma and the commits.
+// A stage (64 frames, sixteen MMAs) is filled by the sixteen producer warps and one TMA copy,
+// all arriving on one `full` barrier, and released by one tcgen05.commit on its `empty`
+// barrier.  The issue loop has no integer division.  Per-stage costs (barrier waits, commits,
+// index bookkeeping) are paid per 64 frames, and the split pre-pass classifies each 16-frame
+// group once (consecutive positions of one scan row or not) for every CTA.
+// TMEM columns: D_re 0-127, D_im 128-255, two A slots of 128 columns at 256-511
+// (slot a, K-step ks, part p: column 256 + 128 a + 32 ks + 8 p; two frames per column).
 // Every mbarrier wait is bounded; a wait that runs out records an error code in *status, the
 // CTA stops issuing work, waits (bounded) for the MMAs it issued and frees its TMEM.
 
@@ -52,14 +57,17 @@ namespace {
 
 constexpr int kTileV = 128;        // scan frequencies per CTA (MMA M, TMEM lanes)
 constexpr int kTileK = 64;         // coefficients per CTA (B rows: 64 hi + 64 lo)
-constexpr int kChunk = 32;         // frames per pipeline stage (two UMMA K-steps of 16)
-constexpr int kProducers = 256;    // warps 0-7
-constexpr int kThreadsTC = 320;    // + TMA warp + MMA warp
-constexpr int kStagesA = 4;        // A stages in TMEM
+constexpr int kChunk = 64;         // frames per pipeline stage (four UMMA K-steps of 16)
+constexpr int kKSteps = kChunk / 16;
+constexpr int kProdWarps = 16;     // warps 0-15: four lane quarters x four K-steps
+constexpr int kProducers = 32 * kProdWarps;
+constexpr int kThreadsTC = kProducers + 64;   // + TMA warp + MMA warp
+constexpr int kStagesA = 4;        // pipeline stages (B slots in shared memory)
+constexpr int kSlotsA = 2;         // A slots in TMEM (128 columns each)
 constexpr int kColsD = 256;        // D_re + D_im
 constexpr int kTmemCols = 512;
 constexpr int kCKStepBytes = 128 * 16 * 2;          // one K-step of the B tile: 128 rows x 16 frames
-constexpr int kCStageBytes = 2 * kCKStepBytes;      // 8 KB per 32-frame stage
+constexpr int kCStageBytes = kKSteps * kCKStepBytes; // 16 KB per 64-frame stage
 constexpr int kTileStride = kTileK * 8 + 16;        // epilogue tile row: 64 float2 + 16 B pad
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
@@ -136,20 +144,6 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t
     }
 }
 
-// 32 consecutive TMEM columns of this thread's lane <- r[0..31], and the wait for the store.
-__device__ __forceinline__ void tmem_st32_wait(uint32_t taddr, const uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n\t"
-        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
-        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
-        "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
-
 // x mod d for x < 2^32 with a precomputed 64-bit reciprocal (Lemire's fast modulo).
 struct FastMod {
     uint64_t M;
@@ -189,13 +183,15 @@ struct TcArgs {
     const float* scale_inv;   // [Kp] 1 / column scale
     unsigned* colmax;         // [K] per-column max |c| (reset here for the next flush)
     const int32_t* idx;       // [n_pad] scan index of each staged frame
+    const int2* grp;          // [n_pad / 16] per 16-frame group: (first scan index, 1 if the 16
+                              // are consecutive positions of one scan row)
     const float2* tw;         // [lcm] exp(-2 pi i m / lcm), FP32 from FP64
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
     int S, K, Sy, Sx, lcm, my, mx;
-    int stages_total;         // 32-frame stages of the flush
+    int stages_total;         // 64-frame stages of the flush
     int seg_stages;           // stages per TMEM accumulation segment
-    int stagesC;              // B pipeline depth
+    int segments;             // ceil(stages_total / seg_stages)
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
@@ -204,36 +200,51 @@ struct TcArgs {
 struct TcLayout {
     size_t c, tile, bar, tmem, scale, total;
 };
-__host__ __device__ inline TcLayout tc_layout(int stagesC) {
+__host__ __device__ inline TcLayout tc_layout() {
     TcLayout L;
     L.c = 0;
-    L.tile = L.c + (size_t)stagesC * kCStageBytes;
+    L.tile = L.c + (size_t)kStagesA * kCStageBytes;
     L.bar = L.tile + (size_t)kTileV * kTileStride;
-    L.tmem = L.bar + 8 * (size_t)(2 * kStagesA + 2 * stagesC + 3);
+    L.tmem = L.bar + 8 * (size_t)(2 * kStagesA + 3);
     L.scale = (L.tmem + 16 + 15) & ~size_t(15);
     L.total = L.scale + 4 * (size_t)kTileK;
     return L;
 }
+// Dynamic shared memory requested per CTA: more than the layout needs, so that no CTA of another
+// kernel that takes tensor memory (a projection) fits beside it and waits for the columns this CTA
+// holds.
+constexpr size_t kTcSmemRequest = 160 * 1024;
 
-// Named barrier among the 256 threads of warps 0-7 (the epilogue phases).
+// Named barrier among the producer threads (the epilogue phases).
 __device__ __forceinline__ void epilogue_barrier() {
-    asm volatile("bar.sync 1, 256;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory");
+}
+
+// Four 4-column TMEM stores of this thread's lane (parts p at t + 8 p) and the wait for them.
+__device__ __forceinline__ void tmem_st4x4_wait(uint32_t t, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%5], {%6,%7,%8,%9};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%10], {%11,%12,%13,%14};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%15], {%16,%17,%18,%19};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(t + 8u), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+        "r"(r[7]), "r"(t + 16u), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(t + 24u),
+        "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int SC = a.stagesC;
-    const TcLayout L = tc_layout(SC);
+    const TcLayout L = tc_layout();
     uint8_t* c_base = base + L.c;
     uint8_t* tile = base + L.tile;
-    uint64_t* fullA = reinterpret_cast<uint64_t*>(base + L.bar);
-    uint64_t* emptyA = fullA + kStagesA;
-    uint64_t* fullC = emptyA + kStagesA;
-    uint64_t* emptyC = fullC + SC;
-    uint64_t* dfull = emptyC + SC;     // a segment's MMAs have completed (MMA warp -> epilogue)
-    uint64_t* dfree = dfull + 1;       // the epilogue has read D (epilogue -> MMA warp)
-    uint64_t* fin = dfree + 1;         // every issued MMA has completed (teardown)
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + L.bar);   // stage filled (A and B)
+    uint64_t* empty = full + kStagesA;                             // stage read by its MMAs
+    uint64_t* dfull = empty + kStagesA;  // a segment's MMAs have completed (MMA warp -> epilogue)
+    uint64_t* dfree = dfull + 1;         // the epilogue has read D (epilogue -> MMA warp)
+    uint64_t* fin = dfree + 1;           // every issued MMA has completed (teardown)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
     float* s_scale = reinterpret_cast<float*>(base + L.scale);
     __shared__ volatile int s_abort;
@@ -243,24 +254,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     const int v0 = blockIdx.x * kTileV;
     const int k0 = blockIdx.y * kTileK;
     const int T = a.stages_total;
-    const int G = (T + a.seg_stages - 1) / a.seg_stages;   // segments
 
     if (threadIdx.x == 0) {
         s_abort = 0;
         for (int s = 0; s < kStagesA; ++s) {
-            mbar_init(&fullA[s], kProducers / 32);   // one arrival per producer warp
-            mbar_init(&emptyA[s], 1);
-        }
-        for (int s = 0; s < SC; ++s) {
-            mbar_init(&fullC[s], 1);
-            mbar_init(&emptyC[s], 1);
+            mbar_init(&full[s], kProdWarps + 1);   // producer warps + the TMA arrival
+            mbar_init(&empty[s], 1);
         }
         mbar_init(dfull, 1);
-        mbar_init(dfree, kProducers / 32);
+        mbar_init(dfree, kProdWarps);
         mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == kProdWarps + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(kTmemCols));
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     // (griddepcontrol.wait) before touching anything this grid writes.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    if (warp < 8) {
+    if (warp < kProdWarps) {
         // ---------------- E producers, and the epilogue between segments ------------------
         const int quarter = warp & 3;
         const int ks = warp >> 2;                       // K-step of each stage this warp fills
@@ -285,39 +291,54 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         const uint32_t vx = (uint32_t)(v % a.Sx);
         const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
         const uint32_t lcm = (uint32_t)a.lcm;
-        // w_v^j = exp(-2 pi i j vx / Sx), j = 0..15, from the table (index j vx mx mod lcm)
-        float2 w[16];
+        // w_v^j = exp(-2 pi i j vx / Sx), j = 0..8, from the table (index j vx mx mod lcm)
+        float2 w[9];
         {
             const uint32_t d = vx * mx;   // < lcm
             uint32_t acc = 0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 9; ++j) {
                 w[j] = __ldg(a.tw + acc);
                 acc += d;
                 if (acc >= lcm) acc -= lcm;
             }
         }
-        const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                (uint32_t)(kColsD + ks * 32);
+        // this warp's 16 frames of stage it form group 4 it + ks; the group records are written
+        // by the split pre-pass.  Records run two stages ahead, the table entry of the group's
+        // first position one stage ahead.
+        const int2* gp = a.grp + ks;
+        int2 g0 = make_int2(0, 0), g1 = g0;
+        float2 b0 = make_float2(1.f, 0.f);
         int ok = 1;   // warp-uniform: this warp has not given up
-        // first and last frame index of this warp's K-step, prefetched one stage ahead
-        const int32_t* ip0 = a.idx + ks * 16;
-        int32_t nf = __ldg(ip0), nl = __ldg(ip0 + 15);
         int it = 0;
-        for (int g = 0; g < G; ++g) {
+        for (int g = 0; g < a.segments; ++g) {
             const int it_end = (g + 1) * a.seg_stages < T ? (g + 1) * a.seg_stages : T;
             for (; it < it_end; ++it) {
-                const int st = it % kStagesA;
-                const int32_t s_first = nf, s_last = nl;
-                if (it + 1 < T) {
-                    const int32_t* ipn = a.idx + (size_t)(it + 1) * kChunk + ks * 16;
-                    nf = __ldg(ipn);
-                    nl = __ldg(ipn + 15);
+                if (it == 0) {
+                    // the records come from the split pre-pass, the launch before this one
+                    asm volatile("griddepcontrol.wait;" ::: "memory");
+                    g0 = __ldg(gp);
+                    if (T > 1) g1 = __ldg(gp + kKSteps);
+                    b0 = __ldg(a.tw + phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx,
+                                                  my, mx, lcm));
                 }
+                const int slot = it & (kSlotsA - 1);
+                // prefetch: table entry of the next stage, record of the one after
+                float2 b1 = b0;
+                int2 g2 = make_int2(0, 0);
+                if (it + 1 < T)
+                    b1 = __ldg(a.tw + phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my,
+                                                  mx, lcm));
+                if (it + 2 < T) g2 = __ldg(gp + (size_t)(it + 2) * kKSteps);
                 if (ok) {
                     int good = 1;
                     if (lane == 0) {
-                        if (it >= kStagesA &&
-                            !mbar_wait(&emptyA[st], ((it / kStagesA) - 1) & 1, a.wait_ns)) {
+                        // the A slot is free once the MMAs of stage it - 2 have completed
+                        if (it >= kSlotsA &&
+                            !mbar_wait(&empty[(it - 2) & (kStagesA - 1)], ((it - 2) >> 2) & 1,
+                                       a.wait_ns)) {
                             atomicExch(a.status, 1u);
                             s_abort = 1;
                         }
@@ -325,39 +346,42 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     }
                     ok = __shfl_sync(0xffffffffu, good, 0);
                 }
-                if (!ok) continue;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float2 e[16];
-                const uint32_t s0 = (uint32_t)s_first;
-                const uint32_t sy0 = fastdiv(s0, a.mod_x);
-                const uint32_t sx0 = s0 - sy0 * Sx;
-                if (s_last == s_first + 15 && sx0 + 15u < Sx) {
-                    // 16 consecutive positions of one scan row: E[v, s0] w^j
-                    const uint32_t m0 = phase_index(s0, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
-                    const float2 b = __ldg(a.tw + m0);
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t tcol = t_lane + (uint32_t)(slot * 128);
+                    // two halves of 8 frames: phase factors, FP16 split, four 4-column stores
+                    float2 bh = b0;                                   // E[v, s0 + 8 hf]
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        e[j] = make_float2(fmaf(b.x, w[j].x, -b.y * w[j].y),
-                                           fmaf(b.x, w[j].y, b.y * w[j].x));
-                } else {
-                    const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16;
+                    for (int hf = 0; hf < 2; ++hf) {
+                        float2 e[8];
+                        if (g0.y) {
+                            // consecutive positions of one scan row: E[v, s0] w^j
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const uint32_t m = phase_index((uint32_t)__ldg(ip + j), vy, vx, a.mod_y,
-                                                       a.mod_x, Sx, my, mx, lcm);
-                        e[j] = __ldg(a.tw + m);
+                            for (int j = 0; j < 8; ++j)
+                                e[j] = make_float2(fmaf(bh.x, w[j].x, -bh.y * w[j].y),
+                                                   fmaf(bh.x, w[j].y, bh.y * w[j].x));
+                        } else {
+                            const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16 + hf * 8;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                e[j] = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy, vx,
+                                                                a.mod_y, a.mod_x, Sx, my, mx, lcm));
+                        }
+                        uint32_t r[16];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 4 frame pairs each
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            split2(e[2 * c].x, e[2 * c + 1].x, r[c], r[4 + c]);
+                            split2(e[2 * c].y, e[2 * c + 1].y, r[8 + c], r[12 + c]);
+                        }
+                        tmem_st4x4_wait(tcol + (uint32_t)(hf * 4), r);
+                        bh = make_float2(fmaf(b0.x, w[8].x, -b0.y * w[8].y),
+                                         fmaf(b0.x, w[8].y, b0.y * w[8].x));
                     }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[it & (kStagesA - 1)]);
                 }
-                uint32_t r[32];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 8 columns of frame pairs each
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    split2(e[2 * c].x, e[2 * c + 1].x, r[c], r[8 + c]);
-                    split2(e[2 * c].y, e[2 * c + 1].y, r[16 + c], r[24 + c]);
-                }
-                tmem_st32_wait(t_lane + (uint32_t)(kColsD + st * 64 + ks * 32), r);
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&fullA[st]);
+                g0 = g1; g1 = g2; b0 = b1;
             }
             // ---------------- epilogue of segment g: H[v, k] += (D[k] + D[64 + k]) / scale ----
             // The scales come from the split pre-pass and H from the previous flush: wait for
@@ -383,24 +407,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 ok = go;
             }
             epilogue_barrier();   // s_scale written; the tile is free
-            const int half = warp >> 2;
             if (go) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
                 float2* trow = reinterpret_cast<float2*>(tile + (size_t)row * kTileStride);
+                const int c0 = (warp >> 2) * 16;   // this warp's 16 coefficient columns
+                float rh[16], rl[16], ih[16], il[16];
+                tmem_ld16x4(tl + (uint32_t)c0, tl + (uint32_t)(64 + c0), tl + (uint32_t)(128 + c0),
+                            tl + (uint32_t)(192 + c0), rh, rl, ih, il);
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int c0 = half * 32 + cc * 16;   // coefficient column within the tile
-                    float rh[16], rl[16], ih[16], il[16];
-                    tmem_ld16x4(t_lane + (uint32_t)c0, t_lane + (uint32_t)(64 + c0),
-                                t_lane + (uint32_t)(128 + c0), t_lane + (uint32_t)(192 + c0),
-                                rh, rl, ih, il);
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const float s0v = s_scale[c0 + i], s1v = s_scale[c0 + i + 1];
-                        *reinterpret_cast<float4*>(trow + c0 + i) =
-                            make_float4((rh[i] + rl[i]) * s0v, (ih[i] + il[i]) * s0v,
-                                        (rh[i + 1] + rl[i + 1]) * s1v, (ih[i + 1] + il[i + 1]) * s1v);
-                    }
+                for (int i = 0; i < 16; i += 2) {
+                    const float s0v = s_scale[c0 + i], s1v = s_scale[c0 + i + 1];
+                    *reinterpret_cast<float4*>(trow + c0 + i) =
+                        make_float4((rh[i] + rl[i]) * s0v, (ih[i] + il[i]) * s0v,
+                                    (rh[i + 1] + rl[i + 1]) * s1v, (ih[i + 1] + il[i + 1]) * s1v);
                 }
                 // D has been read: the next segment's MMAs may overwrite it
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -409,12 +429,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             }
             epilogue_barrier();   // the tile is complete
             if (go) {
-                // warp w updates tile rows w, w + 8, ...; lane l the coefficients l and l + 32
-                for (int vb = 0; vb < kTileV / 8; vb += 4) {
+                // warp w updates tile rows w, w + 16, ...; lane l the coefficients l and l + 32;
+                // the H values of four rows are loaded before any is stored
+#pragma unroll
+                for (int i0 = 0; i0 < kTileV / kProdWarps; i0 += 4) {
                     float2 hv[4][2];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int vv = v0 + warp + 8 * (vb + i);
+                        const int vv = v0 + warp + kProdWarps * (i0 + i);
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             const int k = k0 + hh * 32 + lane;
@@ -424,9 +446,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int vr = warp + 8 * (vb + i);
+                        const int vr = warp + kProdWarps * (i0 + i);
                         const int vv = v0 + vr;
-                        const float2* trow = reinterpret_cast<const float2*>(tile + (size_t)vr * kTileStride);
+                        const float2* trow =
+                            reinterpret_cast<const float2*>(tile + (size_t)vr * kTileStride);
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             const int kl = hh * 32 + lane;
@@ -441,70 +464,74 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 }
             }
         }
-    } else if (warp == 8) {
-        // ---------------- B loader (TMA), running up to SC stages ahead ----------------
+    } else if (warp == kProdWarps) {
+        // ---------------- B loader (TMA) ----------------
         if (lane == 0) {
             // the split coefficients come from the launch before (the split pre-pass)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
                                  (size_t)blockIdx.y * T * kCStageBytes;
             for (int it = 0; it < T; ++it) {
-                const int sc = it % SC;
-                if (it >= SC && !mbar_wait(&emptyC[sc], ((it / SC) - 1) & 1, a.wait_ns)) {
+                const int st = it & (kStagesA - 1);
+                if (it >= kStagesA && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
                     atomicExch(a.status, 2u);
                     s_abort = 1;
                     break;
                 }
                 if (s_abort) break;
-                mbar_arrive_tx(&fullC[sc], kCStageBytes);
-                tma_load_1d(c_base + (size_t)sc * kCStageBytes, src + (size_t)it * kCStageBytes,
-                            kCStageBytes, &fullC[sc]);
+                mbar_arrive_tx(&full[st], kCStageBytes);
+                tma_load_1d(c_base + (size_t)st * kCStageBytes, src + (size_t)it * kCStageBytes,
+                            kCStageBytes, &full[st]);
             }
         }
     } else {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer: no division in this loop ----------------
         if (lane == 0) {
             const uint32_t id_full = instr_desc(128, 2 * kTileK);   // B = [c_hi | c_lo]
             const uint32_t id_hi = instr_desc(128, kTileK);         // B = c_hi
             const uint64_t dc0 = smem_desc(smem_u32(c_base), 128, 256);
             const uint32_t d_re = tmem, d_im = tmem + 128u;
-            int sc = 0;
-            uint32_t pa = 0, pc = 0;
-            int st = 0;
-            bool run = true;
-            for (int it = 0; it < T && run; ++it) {
-                const bool seg_start = (it % a.seg_stages) == 0;
-                if (seg_start && it > 0) {
-                    // the epilogue must have read the previous segment out of D
-                    if (!mbar_wait(dfree, ((it / a.seg_stages) - 1) & 1, a.wait_ns)) {
+            const int seg = a.seg_stages;
+            int st = 0, seg_left = 0, g = 0;
+            uint32_t ph = 0;
+            for (int it = 0; it < T; ++it) {
+                uint32_t acc = 1u;
+                if (seg_left == 0) {
+                    // a new segment: the epilogue must have read the previous one out of D
+                    if (g > 0 && !mbar_wait(dfree, (uint32_t)(g - 1) & 1u, a.wait_ns)) {
                         atomicExch(a.status, 5u);
                         s_abort = 1;
                         break;
                     }
+                    seg_left = seg;
+                    acc = 0u;
                 }
-                if (!mbar_wait(&fullC[sc], pc, a.wait_ns) || !mbar_wait(&fullA[st], pa, a.wait_ns)) {
+                if (!mbar_wait(&full[st], ph, a.wait_ns)) {
                     atomicExch(a.status, 3u);
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t dc = dc0 + (uint64_t)((sc * kCStageBytes) >> 4);
-                const uint32_t ta = tmem + (uint32_t)(kColsD + st * 64);
+                const uint64_t dbs = dc0 + (uint64_t)((st * kCStageBytes) >> 4);
+                const uint32_t as = tmem + (uint32_t)(kColsD + (it & (kSlotsA - 1)) * 128);
 #pragma unroll
-                for (int k2 = 0; k2 < kChunk / 16; ++k2) {
-                    const uint64_t db = dc + (uint64_t)((k2 * kCKStepBytes) >> 4);
-                    const uint32_t a0 = ta + (uint32_t)(k2 * 32);
-                    const uint32_t acc = (seg_start && k2 == 0) ? 0u : 1u;
-                    mma_f16_ts(d_re, a0, db, id_full, acc);          // Re_hi [c_hi | c_lo]
+                for (int k2 = 0; k2 < kKSteps; ++k2) {
+                    const uint64_t db = dbs + (uint64_t)((k2 * kCKStepBytes) >> 4);
+                    const uint32_t a0 = as + (uint32_t)(k2 * 32);
+                    const uint32_t ac = k2 == 0 ? acc : 1u;
+                    mma_f16_ts(d_re, a0, db, id_full, ac);           // Re_hi [c_hi | c_lo]
+                    mma_f16_ts(d_im, a0 + 16u, db, id_full, ac);     // Im_hi [c_hi | c_lo]
                     mma_f16_ts(d_re, a0 + 8u, db, id_hi, 1u);        // Re_lo c_hi
-                    mma_f16_ts(d_im, a0 + 16u, db, id_full, acc);    // Im_hi [c_hi | c_lo]
                     mma_f16_ts(d_im, a0 + 24u, db, id_hi, 1u);       // Im_lo c_hi
                 }
-                mma_commit(&emptyA[st]);   // free both stages once these MMAs have read them
-                mma_commit(&emptyC[sc]);
-                if ((it + 1) % a.seg_stages == 0 || it + 1 == T) mma_commit(dfull);
-                if (++st == kStagesA) { st = 0; pa ^= 1u; }
-                if (++sc == SC) { sc = 0; pc ^= 1u; }
+                mma_commit(&empty[st]);   // frees the stage (A and B) once these MMAs have read it
+                if (--seg_left == 0 || it + 1 == T) {
+                    mma_commit(dfull);
+                    ++g;
+                    seg_left = 0;
+                }
+                st = (st + 1) & (kStagesA - 1);
+                ph ^= (st == 0) ? 1u : 0u;
             }
             // teardown: every MMA issued above completes before TMEM is freed
             mma_commit(fin);
@@ -514,11 +541,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 
     // column maxima for the next flush: reset by the producer warps, which have passed
     // griddepcontrol.wait, i.e. after the split pre-pass has read them
-    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < 8)
+    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < kProdWarps)
         for (int t = threadIdx.x; t < a.K; t += kProducers) a.colmax[t] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 9) {
+    if (warp == kProdWarps + 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
@@ -532,17 +559,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 // Frames beyond n and coefficients beyond K are zero.  One thread per (frame, column).
 __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
-                                   int n, int n_pad, int K, int Kp) {
-    // the accumulation launched next sets up and generates phase factors meanwhile; it reads
-    // this kernel's output only after griddepcontrol.wait.  Its producers read the staged scan
-    // indices at once: that is safe because this kernel is launched without programmatic
-    // serialization, so the projection that wrote them has completed before it started.  (A
-    // programmatic launch of this kernel would have to wait before releasing its dependents.)
+                                   const int32_t* __restrict__ idx, int2* __restrict__ grp,
+                                   int n, int n_pad, int K, int Kp, int Sx) {
+    // the accumulation launched next sets up meanwhile; it reads this kernel's outputs only after
+    // griddepcontrol.wait.  The staged scan indices it reads were written by the projections,
+    // which completed before this kernel started (it is launched without programmatic
+    // serialization).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = t % Kp;
     const int b = t / Kp;
     if (b >= n_pad) return;
+    if (kk == 0 && (b & 15) == 0) {
+        // group record: first scan index, and whether the 16 frames are consecutive positions
+        // of one scan row (frames beyond n have zero coefficients: any record serves them)
+        const int32_t s0 = idx[b];
+        bool run = s0 >= 0 && (s0 % Sx) + 15 < Sx;
+        for (int j = 1; j < 16 && run; ++j) run = idx[b + j] == s0 + j;
+        grp[b >> 4] = make_int2(s0, run ? 1 : 0);
+    }
     float cm = (kk < K) ? __uint_as_float(colmax[kk]) : 0.f;
     int e = 0;
     if (cm > 0.f) frexpf(cm, &e);
@@ -595,17 +630,9 @@ cudaError_t prepare_split_kernels() {
 // Coefficients per CTA.
 int split_tile_n(int /*K*/) { return kTileK; }
 
-// B pipeline depth: as deep as the shared memory allows (up to 16 stages).  The kernel then needs
-// more shared memory than a projection CTA leaves, so no other CTA of a step shares its SM (each
-// would wait for tensor memory this CTA holds).
-static int split_stages_c() {
-    const size_t limit = 226 * 1024 - 1024;   // dynamic bytes after the alignment slack
-    int C = 16;
-    while (C > 2 && tc_layout(C).total > limit) --C;
-    return C;
+size_t split_smem_bytes(int /*NT*/) {
+    return kTcSmemRequest > 1024 + tc_layout().total ? kTcSmemRequest : 1024 + tc_layout().total;
 }
-
-size_t split_smem_bytes(int /*NT*/) { return 1024 + tc_layout(split_stages_c()).total; }
 
 // Kernel launches of one flush: the split pre-pass and the accumulation.
 int split_launch_count(int /*n*/, int /*segment*/) { return 2; }
@@ -625,8 +652,8 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     {
         const size_t total = (size_t)n_pad * Kp;
         split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-            c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, n, n_pad,
-            P->K, Kp);
+            c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, idx,
+            P->d_grp, n, n_pad, P->K, Kp, P->Sx);
     }
     // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
     TcArgs a;
@@ -634,6 +661,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.scale_inv = P->d_scale_inv;
     a.colmax = P->d_colmax;
     a.idx = idx;
+    a.grp = P->d_grp;
     a.tw = P->d_tw;
     a.H = P->d_H;
     a.status = P->d_status;
@@ -646,7 +674,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.mx = P->lcm / P->Sx;
     a.stages_total = n_pad / kChunk;
     a.seg_stages = P->segment / kChunk > 0 ? P->segment / kChunk : 1;
-    a.stagesC = split_stages_c();
+    a.segments = (a.stages_total + a.seg_stages - 1) / a.seg_stages;
     a.wait_ns = kDeviceWaitNs;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
@@ -656,7 +684,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((P->S + kTileV - 1) / kTileV, Kp / kTileK);
     cfg.blockDim = dim3(kThreadsTC, 1, 1);
-    cfg.dynamicSmemBytes = 1024 + tc_layout(a.stagesC).total;
+    cfg.dynamicSmemBytes = split_smem_bytes(kTileK);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

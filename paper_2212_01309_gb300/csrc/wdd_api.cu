@@ -169,6 +169,7 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += 4LL * P->depth * P->K + 4LL * P->depth;            // staging
     b += 16LL * P->S;                                       // spectrum + DFT scratch
     b += 8LL * P->depth_pad * (P->K + 256) + 8LL * P->K;    // FP16 split coefficients
+    b += (int64_t)P->depth_pad / 2;                         // 16-frame group records
     if (P->proj_tc)                                                          // basis image, By
         b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx) + 4LL * ((P->Ny * P->Ly + 3) / 4 * 4);
     if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) {                            // row slots, G
@@ -385,8 +386,8 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
     P->max_batch = p.max_batch;
     P->chunk = std::min(p.max_batch, kLaunchFrames);
     P->depth = p.accum_depth > 0 ? std::max(p.accum_depth, p.max_batch) : p.max_batch;
-    P->depth_pad = (P->depth + 31) / 32 * 32;
-    P->segment = p.accum_segment > 0 ? (p.accum_segment + 31) / 32 * 32 : 1024;
+    P->depth_pad = (P->depth + 63) / 64 * 64;
+    P->segment = p.accum_segment > 0 ? (p.accum_segment + 63) / 64 * 64 : 1024;
     if (p.precision == WDD_PREC_SPLIT && P->depth_pad > 8192) {
         delete P;
         return fail(WDD_ERR_INVALID_ARG, "split precision stages at most 8192 frames");
@@ -534,6 +535,7 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         int Kp = (P->K + NT - 1) / NT * NT;
         WDD_ALLOC(P->d_bsplit, split_coeff_bytes(P->K, P->depth_pad) / 2);
         WDD_ALLOC(P->d_scale_inv, Kp);
+        WDD_ALLOC(P->d_grp, P->depth_pad / 16);
         WDD_ALLOC(P->d_colmax, P->K);
     }
     if (P->proj_tc) {

@@ -101,6 +101,7 @@ struct wdd_plan {
     float2* d_tmp = nullptr;     // [S] inverse-DFT intermediate
     uint16_t* d_bsplit = nullptr;  // split path: FP16 hi/lo coefficients in the UMMA A layout
     float* d_scale_inv = nullptr;  // split path: [Kp] inverse power-of-two column scales
+    int2* d_grp = nullptr;         // split path: [depth_pad / 16] 16-frame group records
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
@@ -113,8 +114,8 @@ struct wdd_plan {
     int32_t* d_frameslot = nullptr; // [depth_pad] slot of each staged frame
     int32_t* d_nslots = nullptr;    // [1] slots in use
     int proj_tc = 0;               // 1: projection on the tensor cores
-    int depth_pad = 0;             // staging depth rounded up to the split kernel's 32-frame stage
-    int segment = 1024;            // split path: frames per tensor-core accumulation launch
+    int depth_pad = 0;             // staging depth rounded up to the split kernel's 64-frame stage
+    int segment = 1024;            // split path: frames per TMEM accumulation segment
     wdd::PendingLaunch pend;       // pushes gathered for one projection launch
 
     // host bookkeeping (exact)
