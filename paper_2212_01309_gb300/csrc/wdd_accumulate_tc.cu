@@ -1,29 +1,31 @@
 // Phase accumulation on the 5th-generation tensor cores (tcgen05, TMEM), split FP16 precision:
 //   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. 14, Algorithm 2)
 //
-// One CTA owns 128 scan frequencies (the MMA's M = 128 rows, one TMEM lane each) and 64
-// coefficients, and runs every staged frame of a flush through them:
-//   A operand (TMEM, M = 128 x K = 16 frames): the phase factors, generated in the kernel and
-//             written straight into tensor memory (tcgen05.st) in four FP16 parts, Re_hi,
-//             Re_lo, Im_hi and Im_lo, so they never pass through shared memory;
-//   B operand (SMEM, N = 128 rows): the 64 coefficients' FP16 hi parts (rows 0-63) and lo parts
-//             (rows 64-127), each column scaled by a power of two first (split_coeff_kernel),
-//             streamed in by 1-D TMA bulk copies.
-// Per 16-frame K-step four MMAs accumulate, in FP32 TMEM,
-//   D_re[v, 0:128] += Re_hi [c_hi | c_lo],   D_re[v, 0:64] += Re_lo c_hi,
-//   D_im[v, 0:128] += Im_hi [c_hi | c_lo],   D_im[v, 0:64] += Im_lo c_hi,
+// One CTA owns 64 scan frequencies and NT = 64 or 128 coefficients and runs every staged frame of
+// a flush through them.  The 128 rows of the MMA (TMEM lanes) hold the real parts of the 64
+// frequencies' phase factors (rows 0-63) and their imaginary parts (rows 64-127):
+//   A operand (TMEM, M = 128 x K = 16 frames): Re or Im of E, generated in the kernel and written
+//             straight into tensor memory (tcgen05.st) as an FP16 hi part and an FP16 lo part, so
+//             it never passes through shared memory;
+//   B operand (SMEM, N = 2 NT rows): the NT coefficients' FP16 hi parts (rows 0 .. NT-1) and lo
+//             parts (rows NT .. 2NT-1), each column scaled by a power of two first
+//             (split_coeff_kernel), streamed in by 1-D TMA bulk copies.
+// Per 16-frame K-step two MMAs accumulate in FP32 TMEM
+//   D[row, 0:2NT] += A_hi [c_hi | c_lo],   D[row, 0:NT] += A_lo c_hi,
 // i.e. (E_hi + E_lo)(c_hi + c_lo) without the lo*lo product, which lies below FP32 rounding
-// (~2^-24 relative): the split carries about 22 significant bits.  The epilogue adds columns
-// k and 64 + k and divides the scale out.
+// (~2^-24 relative): the split carries about 22 significant bits.  The epilogue adds columns k
+// and NT + k, divides the scale out and adds row r (Re) and row 64 + r (Im) into H.
+// Stacking Re and Im in M halves each thread's arithmetic per phase factor, and with NT = 128
+// every generated value feeds an N = 256 MMA.
 //
 // Phase factors: E[v, s] = exp(-2 pi i (v_y s_y / S_y + v_x s_x / S_x)) (the 2-D scan DFT of
-// Eq. 14, separable in the scan axes).  For the 16 frames of a K-step that are consecutive
-// positions of one scan row (raster order), E[v, s0 + j] = E[v, s0] w_v^j with
-// w_v = exp(-2 pi i v_x / S_x): one FP32 table entry (exact integer index
-// m = (v_y s_y mod S_y)(lcm / S_y) + (v_x s_x mod S_x)(lcm / S_x) mod lcm into a table built in
-// FP64) times the powers w_v^j that each thread holds in registers, read once from the same
-// table.  Any other 16 frames take one table entry each.  Both are products of correctly rounded
-// FP32 values, within a few 2^-24 of the FP64 phase factor before the FP16 split.
+// Eq. 14, separable in the scan axes).  For 16 frames at consecutive positions of one scan row
+// (raster order), E[v, s0 + j] = E[v, s0] w_v^j with w_v = exp(-2 pi i v_x / S_x): one FP32 table
+// entry (exact integer index m = (v_y s_y mod S_y)(lcm / S_y) + (v_x s_x mod S_x)(lcm / S_x)
+// mod lcm into a table built in FP64) times powers w_v^j read once from the same table.  The
+// split pre-pass marks each 16-frame group that is such a run; other groups take one table entry
+// per frame.  Both are products of correctly rounded FP32 values, within a few 2^-24 of the FP64
+// phase factor before the FP16 split.
 //
 // Accuracy bookkeeping: TMEM accumulates `seg_stages` stages (accum_segment frames); then the
 // epilogue adds the segment into H in FP32 and the next segment starts a fresh accumulator (the
@@ -31,18 +33,19 @@
 // accumulator).  All segments of a flush run in one launch.
 //
 // Warp roles (576 threads, one CTA per SM: all 512 TMEM columns):
-//   warps 0-15  E producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 (its scan frequencies) for
-//               K-step w / 4 of every 64-frame stage; between segments they run the epilogue
-//               (tcgen05.ld -> shared-memory tile -> coalesced H += (hi + lo) / scale);
+//   warps 0-15  producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 for K-step w / 4 of every
+//               64-frame stage; they also run the epilogue (tcgen05.ld -> FP32 running sums
+//               -> shared-memory tiles -> coalesced H += sum / scale);
 //   warp 16     TMA loader of the B operand;
 //   warp 17     TMEM allocation; one elected lane issues tcgen05.mma and the commits.
-// A stage (64 frames, sixteen MMAs) is filled by the sixteen producer warps and one TMA copy,
-// all arriving on one `full` barrier, and released by one tcgen05.commit on its `empty`
-// barrier.  The issue loop has no integer division.  Per-stage costs (barrier waits, commits,
-// index bookkeeping) are paid per 64 frames, and the split pre-pass classifies each 16-frame
-// group once (consecutive positions of one scan row or not) for every CTA.
-// TMEM columns: D_re 0-127, D_im 128-255, two A slots of 128 columns at 256-511
-// (slot a, K-step ks, part p: column 256 + 128 a + 32 ks + 8 p; two frames per column).
+// A stage (64 frames, eight MMAs) is filled by the sixteen producer warps and one TMA copy, all
+// arriving on one `full` barrier, and released by one tcgen05.commit on its `empty` barrier.
+// The issue loop has no integer division (a single thread's scalar latency bounded an earlier
+// version of this loop, not the tensor pipe).  Between segments each producer thread adds its
+// row of D (hi and lo columns) into FP32 registers, so the MMAs wait only for that read; H is
+// read and written once per flush.
+// TMEM columns: D 0 .. 2NT-1, four A slots of 64 columns from 2NT (slot a, K-step ks: hi part at
+// 2NT + 64 a + 16 ks, lo part 8 columns further; two frames per column).
 // Every mbarrier wait is bounded; a wait that runs out records an error code in *status, the
 // CTA stops issuing work, waits (bounded) for the MMAs it issued and frees its TMEM.
 
@@ -55,20 +58,24 @@ namespace wdd {
 
 namespace {
 
-constexpr int kTileV = 128;        // scan frequencies per CTA (MMA M, TMEM lanes)
-constexpr int kTileK = 64;         // coefficients per CTA (B rows: 64 hi + 64 lo)
+constexpr int kTileV = 64;         // scan frequencies per CTA (Re and Im: MMA M = 128)
 constexpr int kChunk = 64;         // frames per pipeline stage (four UMMA K-steps of 16)
 constexpr int kKSteps = kChunk / 16;
 constexpr int kProdWarps = 16;     // warps 0-15: four lane quarters x four K-steps
 constexpr int kProducers = 32 * kProdWarps;
 constexpr int kThreadsTC = kProducers + 64;   // + TMA warp + MMA warp
-constexpr int kStagesA = 4;        // pipeline stages (B slots in shared memory)
-constexpr int kSlotsA = 2;         // A slots in TMEM (128 columns each)
-constexpr int kColsD = 256;        // D_re + D_im
+constexpr int kStages = 4;         // pipeline stages (A slots in TMEM, B slots in shared memory)
 constexpr int kTmemCols = 512;
-constexpr int kCKStepBytes = 128 * 16 * 2;          // one K-step of the B tile: 128 rows x 16 frames
-constexpr int kCStageBytes = kKSteps * kCKStepBytes; // 16 KB per 64-frame stage
-constexpr int kTileStride = kTileK * 8 + 16;        // epilogue tile row: 64 float2 + 16 B pad
+constexpr size_t kTcSmemRequest = 160 * 1024;
+
+// Coefficient tile geometry.
+template <int NT>
+struct Tile {
+    static constexpr int kKStepBytes = 2 * NT * 16 * 2;        // B: 2 NT rows x 16 frames, FP16
+    static constexpr int kStageBytes = kKSteps * kKStepBytes;
+    static constexpr int kColsD = 2 * NT;
+    static constexpr int kRowBytes = NT * 4 + 16;              // epilogue tile row (floats + pad)
+};
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
 // LBO = byte distance between the two core matrices along K, SBO = between 8-row groups.
@@ -106,44 +113,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         : "memory");
 }
 
-// Four 16-column TMEM loads of this thread's lane (addresses t0..t3) and the wait for them, in one
-// statement, so no use of the destination registers can be scheduled before the wait.
-__device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
-                                            float (&o0)[16], float (&o1)[16], float (&o2)[16],
-                                            float (&o3)[16]) {
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
-        "%28,%29,%30,%31}, [%65];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
-        "%44,%45,%46,%47}, [%66];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,"
-        "%60,%61,%62,%63}, [%67];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
-          "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
-          "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
-          "=r"(r[62]), "=r"(r[63])
-        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        o0[i] = __uint_as_float(r[i]);
-        o1[i] = __uint_as_float(r[16 + i]);
-        o2[i] = __uint_as_float(r[32 + i]);
-        o3[i] = __uint_as_float(r[48 + i]);
-    }
-}
-
 // x mod d for x < 2^32 with a precomputed 64-bit reciprocal (Lemire's fast modulo).
 struct FastMod {
     uint64_t M;
@@ -179,7 +148,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 }
 
 struct TcArgs {
-    const uint16_t* csplit;   // B operand (see split_coeff_kernel), [k-tile][stage][8 KB]
+    const uint16_t* csplit;   // B operand (see split_coeff_kernel), [k-tile][stage][stage bytes]
     const float* scale_inv;   // [Kp] 1 / column scale
     unsigned* colmax;         // [K] per-column max |c| (reset here for the next flush)
     const int32_t* idx;       // [n_pad] scan index of each staged frame
@@ -200,49 +169,79 @@ struct TcArgs {
 struct TcLayout {
     size_t c, tile, bar, tmem, scale, total;
 };
+template <int NT>
 __host__ __device__ inline TcLayout tc_layout() {
     TcLayout L;
     L.c = 0;
-    L.tile = L.c + (size_t)kStagesA * kCStageBytes;
-    L.bar = L.tile + (size_t)kTileV * kTileStride;
-    L.tmem = L.bar + 8 * (size_t)(2 * kStagesA + 3);
+    L.tile = L.c + (size_t)kStages * Tile<NT>::kStageBytes;
+    L.bar = L.tile + 2 * (size_t)kTileV * Tile<NT>::kRowBytes;   // Re and Im tiles
+    L.tmem = L.bar + 8 * (size_t)(2 * kStages + 3);
     L.scale = (L.tmem + 16 + 15) & ~size_t(15);
-    L.total = L.scale + 4 * (size_t)kTileK;
+    L.total = L.scale + 4 * (size_t)NT;
     return L;
 }
-// Dynamic shared memory requested per CTA: more than the layout needs, so that no CTA of another
-// kernel that takes tensor memory (a projection) fits beside it and waits for the columns this CTA
-// holds.
-constexpr size_t kTcSmemRequest = 160 * 1024;
+// Dynamic shared memory requested per CTA: at least kTcSmemRequest, so that no CTA of another
+// kernel that takes tensor memory (a projection) fits beside it and waits for the columns this
+// CTA holds.
+template <int NT>
+inline size_t tc_smem_bytes() {
+    const size_t need = 1024 + tc_layout<NT>().total;
+    return need > kTcSmemRequest ? need : kTcSmemRequest;
+}
 
 // Named barrier among the producer threads (the epilogue phases).
 __device__ __forceinline__ void epilogue_barrier() {
     asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory");
 }
 
-// Four 4-column TMEM stores of this thread's lane (parts p at t + 8 p) and the wait for them.
-__device__ __forceinline__ void tmem_st4x4_wait(uint32_t t, const uint32_t (&r)[16]) {
+// 16 consecutive TMEM columns of this thread's lane <- r[0..15], and the wait for the store.
+__device__ __forceinline__ void tmem_st16_wait(uint32_t t, const uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n\t"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%5], {%6,%7,%8,%9};\n\t"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%10], {%11,%12,%13,%14};\n\t"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%15], {%16,%17,%18,%19};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};\n\t"
         "tcgen05.wait::st.sync.aligned;" ::"r"(t),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(t + 8u), "r"(r[4]), "r"(r[5]), "r"(r[6]),
-        "r"(r[7]), "r"(t + 16u), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(t + 24u),
-        "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
         : "memory");
 }
 
+// Two 16-column TMEM loads of this thread's lane and the wait for them, in one statement.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float (&o0)[16],
+                                            float (&o1)[16]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+        "%28,%29,%30,%31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t0), "r"(t1)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        o0[i] = __uint_as_float(r[i]);
+        o1[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
+template <int NT>
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
+    using TL = Tile<NT>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const TcLayout L = tc_layout();
+    const TcLayout L = tc_layout<NT>();
     uint8_t* c_base = base + L.c;
-    uint8_t* tile = base + L.tile;
+    float* t_re = reinterpret_cast<float*>(base + L.tile);                     // [64][NT + 4]
+    float* t_im = reinterpret_cast<float*>(base + L.tile + (size_t)kTileV * TL::kRowBytes);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + L.bar);   // stage filled (A and B)
-    uint64_t* empty = full + kStagesA;                             // stage read by its MMAs
-    uint64_t* dfull = empty + kStagesA;  // a segment's MMAs have completed (MMA warp -> epilogue)
+    uint64_t* empty = full + kStages;                              // stage read by its MMAs
+    uint64_t* dfull = empty + kStages;   // a segment's MMAs have completed (MMA warp -> epilogue)
     uint64_t* dfree = dfull + 1;         // the epilogue has read D (epilogue -> MMA warp)
     uint64_t* fin = dfree + 1;           // every issued MMA has completed (teardown)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
@@ -252,12 +251,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int v0 = blockIdx.x * kTileV;
-    const int k0 = blockIdx.y * kTileK;
+    const int k0 = blockIdx.y * NT;
     const int T = a.stages_total;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < kStagesA; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], kProdWarps + 1);   // producer warps + the TMA arrival
             mbar_init(&empty[s], 1);
         }
@@ -281,12 +280,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp < kProdWarps) {
-        // ---------------- E producers, and the epilogue between segments ------------------
+        // ---------------- producers, and the epilogue between segments ---------------------
         const int quarter = warp & 3;
         const int ks = warp >> 2;                       // K-step of each stage this warp fills
-        const int row = quarter * 32 + lane;            // TMEM lane = frequency in the tile
+        const bool imag = quarter >= 2;                 // rows 64-127: imaginary parts
+        const int vi = (quarter & 1) * 32 + lane;       // frequency within the tile
         // Rows beyond S (last tile) generate v = 0; the epilogue never writes them.
-        const int v = (v0 + row < a.S) ? v0 + row : 0;
+        const int v = (v0 + vi < a.S) ? v0 + vi : 0;
         const uint32_t vy = (uint32_t)(v / a.Sx);
         const uint32_t vx = (uint32_t)(v % a.Sx);
         const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
@@ -304,7 +304,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             }
         }
         const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                (uint32_t)(kColsD + ks * 32);
+                                (uint32_t)(TL::kColsD + ks * 16);
+        // running sums of this thread's row (Re or Im of frequency vi) over the segments, for
+        // coefficient columns cbase .. cbase + NT / 4 - 1 of the tile (FP32)
+        const int cbase = ks * (NT / 4);
+        float sum[NT / 4];
+#pragma unroll
+        for (int i = 0; i < NT / 4; ++i) sum[i] = 0.f;
         // this warp's 16 frames of stage it form group 4 it + ks; the group records are written
         // by the split pre-pass.  Records run two stages ahead, the table entry of the group's
         // first position one stage ahead.
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     b0 = __ldg(a.tw + phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx,
                                                   my, mx, lcm));
                 }
-                const int slot = it & (kSlotsA - 1);
+                const int st = it & (kStages - 1);
                 // prefetch: table entry of the next stage, record of the one after
                 float2 b1 = b0;
                 int2 g2 = make_int2(0, 0);
@@ -335,10 +341,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 if (ok) {
                     int good = 1;
                     if (lane == 0) {
-                        // the A slot is free once the MMAs of stage it - 2 have completed
-                        if (it >= kSlotsA &&
-                            !mbar_wait(&empty[(it - 2) & (kStagesA - 1)], ((it - 2) >> 2) & 1,
-                                       a.wait_ns)) {
+                        // the slot is free once the MMAs of stage it - 4 have completed
+                        if (it >= kStages &&
+                            !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
                             atomicExch(a.status, 1u);
                             s_abort = 1;
                         }
@@ -348,50 +353,46 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 }
                 if (ok) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t tcol = t_lane + (uint32_t)(slot * 128);
-                    // two halves of 8 frames: phase factors, FP16 split, four 4-column stores
-                    float2 bh = b0;                                   // E[v, s0 + 8 hf]
+                    // Re or Im of the 16 phase factors, two halves of 8 frames
+                    float x[16];
+                    if (g0.y) {
+                        // consecutive positions of one scan row: E[v, s0] w^j, E[v, s0 + 8] w^j
+                        const float2 b8 = make_float2(fmaf(b0.x, w[8].x, -b0.y * w[8].y),
+                                                      fmaf(b0.x, w[8].y, b0.y * w[8].x));
+                        if (imag) {
 #pragma unroll
-                    for (int hf = 0; hf < 2; ++hf) {
-                        float2 e[8];
-                        if (g0.y) {
-                            // consecutive positions of one scan row: E[v, s0] w^j
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                e[j] = make_float2(fmaf(bh.x, w[j].x, -bh.y * w[j].y),
-                                                   fmaf(bh.x, w[j].y, bh.y * w[j].x));
+                            for (int j = 0; j < 8; ++j) {
+                                x[j] = fmaf(b0.x, w[j].y, b0.y * w[j].x);
+                                x[8 + j] = fmaf(b8.x, w[j].y, b8.y * w[j].x);
+                            }
                         } else {
-                            const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16 + hf * 8;
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                e[j] = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy, vx,
-                                                                a.mod_y, a.mod_x, Sx, my, mx, lcm));
+                            for (int j = 0; j < 8; ++j) {
+                                x[j] = fmaf(b0.x, w[j].x, -b0.y * w[j].y);
+                                x[8 + j] = fmaf(b8.x, w[j].x, -b8.y * w[j].y);
+                            }
                         }
-                        uint32_t r[16];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 4 frame pairs each
+                    } else {
+                        const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16;
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            split2(e[2 * c].x, e[2 * c + 1].x, r[c], r[4 + c]);
-                            split2(e[2 * c].y, e[2 * c + 1].y, r[8 + c], r[12 + c]);
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 e = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy,
+                                                                      vx, a.mod_y, a.mod_x, Sx, my,
+                                                                      mx, lcm));
+                            x[j] = imag ? e.y : e.x;
                         }
-                        tmem_st4x4_wait(tcol + (uint32_t)(hf * 4), r);
-                        bh = make_float2(fmaf(b0.x, w[8].x, -b0.y * w[8].y),
-                                         fmaf(b0.x, w[8].y, b0.y * w[8].x));
                     }
+                    uint32_t r[16];   // hi part (8 frame pairs), then lo part
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) split2(x[2 * c], x[2 * c + 1], r[c], r[8 + c]);
+                    tmem_st16_wait(t_lane + (uint32_t)(st * 64), r);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&full[it & (kStagesA - 1)]);
+                    if (lane == 0) mbar_arrive(&full[st]);
                 }
                 g0 = g1; g1 = g2; b0 = b1;
             }
-            // ---------------- epilogue of segment g: H[v, k] += (D[k] + D[64 + k]) / scale ----
-            // The scales come from the split pre-pass and H from the previous flush: wait for
-            // the launch before this one (a no-op after the first time).
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-            if (g == 0)
-                for (int t = threadIdx.x; t < kTileK; t += kProducers) {
-                    const int k = k0 + t;
-                    s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
-                }
+            // ---------------- end of segment g: D is added into this thread's running sums ------
             int go = 0;
             if (ok) {
                 int good = 1;
@@ -406,61 +407,67 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                 go = __shfl_sync(0xffffffffu, good, 0);
                 ok = go;
             }
-            epilogue_barrier();   // s_scale written; the tile is free
             if (go) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-                float2* trow = reinterpret_cast<float2*>(tile + (size_t)row * kTileStride);
-                const int c0 = (warp >> 2) * 16;   // this warp's 16 coefficient columns
-                float rh[16], rl[16], ih[16], il[16];
-                tmem_ld16x4(tl + (uint32_t)c0, tl + (uint32_t)(64 + c0), tl + (uint32_t)(128 + c0),
-                            tl + (uint32_t)(192 + c0), rh, rl, ih, il);
 #pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const float s0v = s_scale[c0 + i], s1v = s_scale[c0 + i + 1];
-                    *reinterpret_cast<float4*>(trow + c0 + i) =
-                        make_float4((rh[i] + rl[i]) * s0v, (ih[i] + il[i]) * s0v,
-                                    (rh[i + 1] + rl[i + 1]) * s1v, (ih[i + 1] + il[i + 1]) * s1v);
+                for (int h = 0; h < NT / 64; ++h) {
+                    const int c0 = cbase + 16 * h;
+                    float hi[16], lo[16];
+                    tmem_ld16x2(tl + (uint32_t)c0, tl + (uint32_t)(NT + c0), hi, lo);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) sum[16 * h + i] += hi[i] + lo[i];
                 }
                 // D has been read: the next segment's MMAs may overwrite it
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(dfree);
             }
-            epilogue_barrier();   // the tile is complete
-            if (go) {
-                // warp w updates tile rows w, w + 16, ...; lane l the coefficients l and l + 32;
-                // the H values of four rows are loaded before any is stored
+        }
+        // ---------------- epilogue: H[v, k] += sum / scale, once per flush ------------------
+        // The scales come from the split pre-pass and H from the previous flush (both complete:
+        // the producers passed griddepcontrol.wait at stage 0).
+        for (int t = threadIdx.x; t < NT; t += kProducers) {
+            const int k = k0 + t;
+            s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+        }
+        epilogue_barrier();   // s_scale written
+        if (ok) {
+            float* trow = (imag ? t_im : t_re) + (size_t)vi * (TL::kRowBytes / 4);
 #pragma unroll
-                for (int i0 = 0; i0 < kTileV / kProdWarps; i0 += 4) {
-                    float2 hv[4][2];
+            for (int i = 0; i < NT / 4; i += 4)
+                *reinterpret_cast<float4*>(trow + cbase + i) = make_float4(
+                    sum[i] * s_scale[cbase + i], sum[i + 1] * s_scale[cbase + i + 1],
+                    sum[i + 2] * s_scale[cbase + i + 2], sum[i + 3] * s_scale[cbase + i + 3]);
+        }
+        epilogue_barrier();   // the tiles are complete
+        if (ok) {
+            // warp w updates rows w, w + 16, w + 32, w + 48; lane l the coefficients l + 32 j
+            constexpr int J = NT / 32;
+            float2 hv[kTileV / kProdWarps][J];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int vv = v0 + warp + kProdWarps * (i0 + i);
+            for (int i = 0; i < kTileV / kProdWarps; ++i) {
+                const int vv = v0 + warp + kProdWarps * i;
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int k = k0 + hh * 32 + lane;
-                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
-                                                              : make_float2(0.f, 0.f);
-                        }
-                    }
+                for (int j = 0; j < J; ++j) {
+                    const int k = k0 + j * 32 + lane;
+                    hv[i][j] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                                                     : make_float2(0.f, 0.f);
+                }
+            }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int vr = warp + kProdWarps * (i0 + i);
-                        const int vv = v0 + vr;
-                        const float2* trow =
-                            reinterpret_cast<const float2*>(tile + (size_t)vr * kTileStride);
+            for (int i = 0; i < kTileV / kProdWarps; ++i) {
+                const int vr = warp + kProdWarps * i;
+                const int vv = v0 + vr;
+                const float* rre = t_re + (size_t)vr * (TL::kRowBytes / 4);
+                const float* rim = t_im + (size_t)vr * (TL::kRowBytes / 4);
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int kl = hh * 32 + lane;
-                            const int k = k0 + kl;
-                            if (vv < a.S && k < a.K) {
-                                const float2 x = trow[kl];
-                                a.H[(size_t)vv * a.K + k] =
-                                    make_float2(hv[i][hh].x + x.x, hv[i][hh].y + x.y);
-                            }
-                        }
-                    }
+                for (int j = 0; j < J; ++j) {
+                    const int kl = j * 32 + lane;
+                    const int k = k0 + kl;
+                    if (vv < a.S && k < a.K)
+                        a.H[(size_t)vv * a.K + k] =
+                            make_float2(hv[i][j].x + rre[kl], hv[i][j].y + rim[kl]);
                 }
             }
         }
@@ -470,27 +477,26 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             // the split coefficients come from the launch before (the split pre-pass)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
-                                 (size_t)blockIdx.y * T * kCStageBytes;
+                                 (size_t)blockIdx.y * T * TL::kStageBytes;
             for (int it = 0; it < T; ++it) {
-                const int st = it & (kStagesA - 1);
-                if (it >= kStagesA && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
+                const int st = it & (kStages - 1);
+                if (it >= kStages && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
                     atomicExch(a.status, 2u);
                     s_abort = 1;
                     break;
                 }
                 if (s_abort) break;
-                mbar_arrive_tx(&full[st], kCStageBytes);
-                tma_load_1d(c_base + (size_t)st * kCStageBytes, src + (size_t)it * kCStageBytes,
-                            kCStageBytes, &full[st]);
+                mbar_arrive_tx(&full[st], TL::kStageBytes);
+                tma_load_1d(c_base + (size_t)st * TL::kStageBytes,
+                            src + (size_t)it * TL::kStageBytes, TL::kStageBytes, &full[st]);
             }
         }
     } else {
         // ---------------- MMA issuer: no division in this loop ----------------
         if (lane == 0) {
-            const uint32_t id_full = instr_desc(128, 2 * kTileK);   // B = [c_hi | c_lo]
-            const uint32_t id_hi = instr_desc(128, kTileK);         // B = c_hi
+            const uint32_t id_full = instr_desc(128, 2 * NT);   // B = [c_hi | c_lo]
+            const uint32_t id_hi = instr_desc(128, NT);         // B = c_hi
             const uint64_t dc0 = smem_desc(smem_u32(c_base), 128, 256);
-            const uint32_t d_re = tmem, d_im = tmem + 128u;
             const int seg = a.seg_stages;
             int st = 0, seg_left = 0, g = 0;
             uint32_t ph = 0;
@@ -512,17 +518,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t dbs = dc0 + (uint64_t)((st * kCStageBytes) >> 4);
-                const uint32_t as = tmem + (uint32_t)(kColsD + (it & (kSlotsA - 1)) * 128);
+                const uint64_t dbs = dc0 + (uint64_t)((st * TL::kStageBytes) >> 4);
+                const uint32_t as = tmem + (uint32_t)(TL::kColsD + st * 64);
 #pragma unroll
                 for (int k2 = 0; k2 < kKSteps; ++k2) {
-                    const uint64_t db = dbs + (uint64_t)((k2 * kCKStepBytes) >> 4);
-                    const uint32_t a0 = as + (uint32_t)(k2 * 32);
-                    const uint32_t ac = k2 == 0 ? acc : 1u;
-                    mma_f16_ts(d_re, a0, db, id_full, ac);           // Re_hi [c_hi | c_lo]
-                    mma_f16_ts(d_im, a0 + 16u, db, id_full, ac);     // Im_hi [c_hi | c_lo]
-                    mma_f16_ts(d_re, a0 + 8u, db, id_hi, 1u);        // Re_lo c_hi
-                    mma_f16_ts(d_im, a0 + 24u, db, id_hi, 1u);       // Im_lo c_hi
+                    const uint64_t db = dbs + (uint64_t)((k2 * TL::kKStepBytes) >> 4);
+                    const uint32_t a0 = as + (uint32_t)(k2 * 16);
+                    mma_f16_ts(tmem, a0, db, id_full, k2 == 0 ? acc : 1u);   // A_hi [c_hi | c_lo]
+                    mma_f16_ts(tmem, a0 + 8u, db, id_hi, 1u);                // A_lo c_hi
                 }
                 mma_commit(&empty[st]);   // frees the stage (A and B) once these MMAs have read it
                 if (--seg_left == 0 || it + 1 == T) {
@@ -530,7 +533,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     ++g;
                     seg_left = 0;
                 }
-                st = (st + 1) & (kStagesA - 1);
+                st = (st + 1) & (kStages - 1);
                 ph ^= (st == 0) ? 1u : 0u;
             }
             // teardown: every MMA issued above completes before TMEM is freed
@@ -553,18 +556,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 }
 
 // Splits the staged FP32 coefficients into FP16 hi/lo parts with a power-of-two scale per column
-// and writes them as the B operand of accumulate_tc_kernel, K-major core matrices:
-//   [k-tile of 64][stage][K-step][row group][core matrix b/8 % 2][row % 8][b % 8]
-// where rows 0-63 of a k-tile hold its 64 coefficients' hi parts and rows 64-127 their lo parts.
-// Frames beyond n and coefficients beyond K are zero.  One thread per (frame, column).
+// and writes them as the B operand of accumulate_tc_kernel<NT>, K-major core matrices:
+//   [k-tile of NT][K-step of 16 frames][row group][core matrix b/8 % 2][row % 8][b % 8]
+// where rows 0 .. NT-1 of a k-tile hold its coefficients' hi parts and rows NT .. 2NT-1 their lo
+// parts (four consecutive K-steps form a 64-frame stage).  Frames beyond n and coefficients
+// beyond K are zero.  One thread per (frame, column).  The thread of column 0 of every 16th frame
+// also writes that 16-frame group's record.
 __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
                                    uint16_t* __restrict__ out, float* __restrict__ scale_inv,
                                    const int32_t* __restrict__ idx, int2* __restrict__ grp,
-                                   int n, int n_pad, int K, int Kp, int Sx) {
+                                   int n, int n_pad, int K, int Kp, int NT, int Sx) {
     // the accumulation launched next sets up meanwhile; it reads this kernel's outputs only after
-    // griddepcontrol.wait.  The staged scan indices it reads were written by the projections,
-    // which completed before this kernel started (it is launched without programmatic
-    // serialization).
+    // griddepcontrol.wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = t % Kp;
@@ -586,13 +589,11 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
     const float x = (b < n && kk < K) ? c[(size_t)b * K + kk] * sc : 0.f;
     const __half hi = __float2half_rn(x);
     const __half lo = __float2half_rn(x - __half2float(hi));
-    const int ktile = kk / kTileK, km = kk % kTileK;
-    const int stage = b / kChunk, bs = b % kChunk;
-    const int ks = bs / 16, bk = bs % 16;
-    const int stages_total = n_pad / kChunk;
-    const size_t base = ((size_t)ktile * stages_total + stage) * (kCStageBytes / 2) +
-                        (size_t)ks * (kCKStepBytes / 2);
-    const int rh = km, rl = 64 + km;
+    const int ktile = kk / NT, km = kk % NT;
+    const int kstep = b >> 4, bk = b & 15;
+    const int ksteps_total = n_pad >> 4;
+    const size_t base = ((size_t)ktile * ksteps_total + kstep) * (size_t)(2 * NT * 16);
+    const int rh = km, rl = NT + km;
     const size_t in_hi = (size_t)(rh >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rh & 7) * 8 + (bk & 7);
     const size_t in_lo = (size_t)(rl >> 3) * 128 + (size_t)(bk >> 3) * 64 + (size_t)(rl & 7) * 8 + (bk & 7);
     out[base + in_hi] = __half_as_ushort(hi);
@@ -624,36 +625,40 @@ cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cud
 bool split_path_available() { return true; }
 
 cudaError_t prepare_split_kernels() {
-    return allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<64>));
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<128>));
+    return e;
 }
 
-// Coefficients per CTA.
-int split_tile_n(int /*K*/) { return kTileK; }
+// Coefficients per CTA: 64 up to K = 64, else 128.
+int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
 
-size_t split_smem_bytes(int /*NT*/) {
-    return kTcSmemRequest > 1024 + tc_layout().total ? kTcSmemRequest : 1024 + tc_layout().total;
-}
+size_t split_smem_bytes(int NT) { return NT == 64 ? tc_smem_bytes<64>() : tc_smem_bytes<128>(); }
 
 // Kernel launches of one flush: the split pre-pass and the accumulation.
 int split_launch_count(int /*n*/, int /*segment*/) { return 2; }
 
 size_t split_coeff_bytes(int K, int depth_pad) {
-    const int Kp = (K + kTileK - 1) / kTileK * kTileK;
+    const int NT = split_tile_n(K);
+    const int Kp = (K + NT - 1) / NT * NT;
     return (size_t)Kp * depth_pad * 2 * 2;   // hi and lo halves
 }
 
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const int Kp = (P->K + kTileK - 1) / kTileK * kTileK;
+    const int NT = split_tile_n(P->K);
+    const int Kp = (P->K + NT - 1) / NT * NT;
     const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
     if (n_pad > P->depth_pad) return cudaErrorInvalidValue;
-    // 1. split the coefficients (per-column scale from the projection's running max)
+    // 1. split the coefficients (per-column scale from the projection's running max) and mark
+    //    the 16-frame groups
     {
         const size_t total = (size_t)n_pad * Kp;
         split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
             c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, idx,
-            P->d_grp, n, n_pad, P->K, Kp, P->Sx);
+            P->d_grp, n, n_pad, P->K, Kp, NT, P->Sx);
     }
     // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
     TcArgs a;
@@ -679,19 +684,20 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
     // the launch overlaps the split pre-pass (programmatic dependent launch): it allocates
-    // tensor memory and generates phase factors meanwhile, and loads the split coefficients and
-    // scales, and touches H, only after griddepcontrol.wait
+    // tensor memory and reads the phase table meanwhile, and reads the group records, the split
+    // coefficients, the scales and H only after griddepcontrol.wait
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((P->S + kTileV - 1) / kTileV, Kp / kTileK);
+    cfg.gridDim = dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
     cfg.blockDim = dim3(kThreadsTC, 1, 1);
-    cfg.dynamicSmemBytes = split_smem_bytes(kTileK);
+    cfg.dynamicSmemBytes = split_smem_bytes(NT);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, accumulate_tc_kernel, a);
+    cudaError_t e = NT == 64 ? cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<64>, a)
+                             : cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<128>, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
