@@ -1,8 +1,8 @@
 // Phase accumulation on the 5th-generation tensor cores (tcgen05, TMEM), split FP16 precision:
 //   H[v, k] += sum_b E[v, s_b] c_b[k],  E = exp(-2 pi i m / lcm)  (Eq. 14, Algorithm 2)
 //
-// One CTA owns 64 scan frequencies and NT = 64 or 128 coefficients and runs every staged frame of
-// a flush through them.  The 128 rows of the MMA (TMEM lanes) hold the real parts of the 64
+// For K > 64 one CTA owns 64 scan frequencies and NT = 128 coefficients and runs every staged
+// frame of a flush through them (K <= 64: accumulate_narrow_kernel below).  The 128 rows of the MMA (TMEM lanes) hold the real parts of the 64
 // frequencies' phase factors (rows 0-63) and their imaginary parts (rows 64-127):
 //   A operand (TMEM, M = 128 x K = 16 frames): Re or Im of E, generated in the kernel and written
 //             straight into tensor memory (tcgen05.st) as an FP16 hi part and an FP16 lo part, so
@@ -152,8 +152,9 @@ struct TcArgs {
     const float* scale_inv;   // [Kp] 1 / column scale
     unsigned* colmax;         // [K] per-column max |c| (reset here for the next flush)
     const int32_t* idx;       // [n_pad] scan index of each staged frame
-    const int2* grp;          // [n_pad / 16] per 16-frame group: (first scan index, 1 if the 16
-                              // are consecutive positions of one scan row)
+    const int2* grp;          // [n_pad / 16] per 16-frame group: (first scan index s0,
+                              // (s0 mod S_x) << 1 | 1 if the 16 are consecutive positions of
+                              // one scan row)
     const float2* tw;         // [lcm] exp(-2 pi i m / lcm), FP32 from FP64
     float2* H;                // [S][K]
     unsigned* status;         // error word (0 = ok)
@@ -315,7 +316,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         // by the split pre-pass.  Records run two stages ahead, the table entry of the group's
         // first position one stage ahead.
         const int2* gp = a.grp + ks;
+        // phase-index step between a group and the group 64 positions further along the same
+        // scan row: (64 vx mod Sx) mx mod lcm
+        const uint32_t d64 = fastmod(64u * vx, a.mod_x) * mx;   // < lcm
         int2 g0 = make_int2(0, 0), g1 = g0;
+        uint32_t m0 = 0;
         float2 b0 = make_float2(1.f, 0.f);
         int ok = 1;   // warp-uniform: this warp has not given up
         int it = 0;
@@ -327,16 +332,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     asm volatile("griddepcontrol.wait;" ::: "memory");
                     g0 = __ldg(gp);
                     if (T > 1) g1 = __ldg(gp + kKSteps);
-                    b0 = __ldg(a.tw + phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx,
-                                                  my, mx, lcm));
+                    m0 = phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
+                    b0 = __ldg(a.tw + m0);
                 }
                 const int st = it & (kStages - 1);
-                // prefetch: table entry of the next stage, record of the one after
+                // prefetch: table entry of the next stage (its index one step along the row from
+                // this one's in raster order), record of the one after
                 float2 b1 = b0;
+                uint32_t m1 = m0;
                 int2 g2 = make_int2(0, 0);
-                if (it + 1 < T)
-                    b1 = __ldg(a.tw + phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my,
-                                                  mx, lcm));
+                if (it + 1 < T) {
+                    if (g1.x == g0.x + 64 && (g1.y >> 1) == (g0.y >> 1) + 64) {
+                        m1 = m0 + d64;
+                        if (m1 >= lcm) m1 -= lcm;
+                    } else {
+                        m1 = phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
+                    }
+                    b1 = __ldg(a.tw + m1);
+                }
                 if (it + 2 < T) g2 = __ldg(gp + (size_t)(it + 2) * kKSteps);
                 if (ok) {
                     int good = 1;
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     // Re or Im of the 16 phase factors, two halves of 8 frames
                     float x[16];
-                    if (g0.y) {
+                    if (g0.y & 1) {
                         // consecutive positions of one scan row: E[v, s0] w^j, E[v, s0 + 8] w^j
                         const float2 b8 = make_float2(fmaf(b0.x, w[8].x, -b0.y * w[8].y),
                                                       fmaf(b0.x, w[8].y, b0.y * w[8].x));
@@ -390,7 +403,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full[st]);
                 }
-                g0 = g1; g1 = g2; b0 = b1;
+                g0 = g1; g1 = g2; b0 = b1; m0 = m1;
             }
             // ---------------- end of segment g: D is added into this thread's running sums ------
             int go = 0;
@@ -555,6 +568,374 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
     }
 }
 
+// ---- K <= 64: 128 frequencies x 64 coefficients per CTA ----------------------------------------
+// For K <= 64 a CTA keeps 128 frequencies in the MMA rows and the real and imaginary parts in two
+// accumulators instead: D_re = Re E [c_hi | c_lo] (TMEM columns 0-127), D_im = Im E [...]
+// (128-255), four MMAs per K-step, two A slots of 128 columns at 256-511 (slot a, K-step ks, part
+// p of Re_hi, Re_lo, Im_hi, Im_lo: column 256 + 128 a + 32 ks + 8 p).  With 64 coefficients this
+// halves the CTAs (and their per-stage costs) for the same work; the stacked layout above only
+// pays off when the generated values feed N = 256 MMAs.
+constexpr int kNarrowV = 128;
+constexpr int kNarrowK = 64;
+constexpr int kNarrowColsD = 256;
+constexpr int kSlotsA = 2;
+constexpr int kNarrowStride = kNarrowK * 8 + 16;   // epilogue tile row: 64 float2 + 16 B pad
+
+__host__ __device__ inline TcLayout narrow_layout() {
+    TcLayout L;
+    L.c = 0;
+    L.tile = L.c + (size_t)kStages * Tile<64>::kStageBytes;
+    L.bar = L.tile + (size_t)kNarrowV * kNarrowStride;
+    L.tmem = L.bar + 8 * (size_t)(2 * kStages + 3);
+    L.scale = (L.tmem + 16 + 15) & ~size_t(15);
+    L.total = L.scale + 4 * (size_t)kNarrowK;
+    return L;
+}
+inline size_t narrow_smem_bytes() {
+    const size_t need = 1024 + narrow_layout().total;
+    return need > kTcSmemRequest ? need : kTcSmemRequest;
+}
+
+// Four 4-column TMEM stores of this thread's lane (parts p at t + 8 p) and the wait for them.
+__device__ __forceinline__ void tmem_st4x4_wait(uint32_t t, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%5], {%6,%7,%8,%9};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%10], {%11,%12,%13,%14};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%15], {%16,%17,%18,%19};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(t + 8u), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+        "r"(r[7]), "r"(t + 16u), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(t + 24u),
+        "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+// Four 16-column TMEM loads of this thread's lane and the wait for them, in one statement.
+__device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
+                                            float (&o0)[16], float (&o1)[16], float (&o2)[16],
+                                            float (&o3)[16]) {
+    tmem_ld16x2(t0, t1, o0, o1);
+    tmem_ld16x2(t2, t3, o2, o3);
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const TcArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const TcLayout L = narrow_layout();
+    uint8_t* c_base = base + L.c;
+    uint8_t* tile = base + L.tile;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + L.bar);   // stage filled (A and B)
+    uint64_t* empty = full + kStages;                             // stage read by its MMAs
+    uint64_t* dfull = empty + kStages;  // a segment's MMAs have completed (MMA warp -> epilogue)
+    uint64_t* dfree = dfull + 1;         // the epilogue has read D (epilogue -> MMA warp)
+    uint64_t* fin = dfree + 1;           // every issued MMA has completed (teardown)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.tmem);
+    float* s_scale = reinterpret_cast<float*>(base + L.scale);
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int v0 = blockIdx.x * kNarrowV;
+    const int k0 = blockIdx.y * kNarrowK;
+    const int T = a.stages_total;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], kProdWarps + 1);   // producer warps + the TMA arrival
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(dfull, 1);
+        mbar_init(dfree, kProdWarps);
+        mbar_init(fin, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kProdWarps + 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    // The next launch may start now (this CTA holds its tensor memory): it waits
+    // (griddepcontrol.wait) before touching anything this grid writes.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    if (warp < kProdWarps) {
+        // ---------------- E producers, and the epilogue between segments ------------------
+        const int quarter = warp & 3;
+        const int ks = warp >> 2;                       // K-step of each stage this warp fills
+        const int row = quarter * 32 + lane;            // TMEM lane = frequency in the tile
+        // Rows beyond S (last tile) generate v = 0; the epilogue never writes them.
+        const int v = (v0 + row < a.S) ? v0 + row : 0;
+        const uint32_t vy = (uint32_t)(v / a.Sx);
+        const uint32_t vx = (uint32_t)(v % a.Sx);
+        const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
+        const uint32_t lcm = (uint32_t)a.lcm;
+        // w_v^j = exp(-2 pi i j vx / Sx), j = 0..8, from the table (index j vx mx mod lcm)
+        float2 w[9];
+        {
+            const uint32_t d = vx * mx;   // < lcm
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                w[j] = __ldg(a.tw + acc);
+                acc += d;
+                if (acc >= lcm) acc -= lcm;
+            }
+        }
+        const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                (uint32_t)(kNarrowColsD + ks * 32);
+        // this warp's 16 frames of stage it form group 4 it + ks; the group records are written
+        // by the split pre-pass.  Records run two stages ahead, the table entry of the group's
+        // first position one stage ahead.
+        const int2* gp = a.grp + ks;
+        int2 g0 = make_int2(0, 0), g1 = g0;
+        float2 b0 = make_float2(1.f, 0.f);
+        int ok = 1;   // warp-uniform: this warp has not given up
+        int it = 0;
+        for (int g = 0; g < a.segments; ++g) {
+            const int it_end = (g + 1) * a.seg_stages < T ? (g + 1) * a.seg_stages : T;
+            for (; it < it_end; ++it) {
+                if (it == 0) {
+                    // the records come from the split pre-pass, the launch before this one
+                    asm volatile("griddepcontrol.wait;" ::: "memory");
+                    g0 = __ldg(gp);
+                    if (T > 1) g1 = __ldg(gp + kKSteps);
+                    b0 = __ldg(a.tw + phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx,
+                                                  my, mx, lcm));
+                }
+                const int slot = it & (kSlotsA - 1);
+                // prefetch: table entry of the next stage, record of the one after
+                float2 b1 = b0;
+                int2 g2 = make_int2(0, 0);
+                if (it + 1 < T)
+                    b1 = __ldg(a.tw + phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my,
+                                                  mx, lcm));
+                if (it + 2 < T) g2 = __ldg(gp + (size_t)(it + 2) * kKSteps);
+                if (ok) {
+                    int good = 1;
+                    if (lane == 0) {
+                        // the A slot is free once the MMAs of stage it - 2 have completed
+                        if (it >= kSlotsA &&
+                            !mbar_wait(&empty[(it - 2) & (kStages - 1)], ((it - 2) >> 2) & 1,
+                                       a.wait_ns)) {
+                            atomicExch(a.status, 1u);
+                            s_abort = 1;
+                        }
+                        good = !s_abort;
+                    }
+                    ok = __shfl_sync(0xffffffffu, good, 0);
+                }
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t tcol = t_lane + (uint32_t)(slot * 128);
+                    // two halves of 8 frames: phase factors, FP16 split, four 4-column stores
+                    float2 bh = b0;                                   // E[v, s0 + 8 hf]
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        float2 e[8];
+                        if (g0.y & 1) {
+                            // consecutive positions of one scan row: E[v, s0] w^j
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                e[j] = make_float2(fmaf(bh.x, w[j].x, -bh.y * w[j].y),
+                                                   fmaf(bh.x, w[j].y, bh.y * w[j].x));
+                        } else {
+                            const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16 + hf * 8;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                e[j] = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy, vx,
+                                                                a.mod_y, a.mod_x, Sx, my, mx, lcm));
+                        }
+                        uint32_t r[16];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 4 frame pairs each
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            split2(e[2 * c].x, e[2 * c + 1].x, r[c], r[4 + c]);
+                            split2(e[2 * c].y, e[2 * c + 1].y, r[8 + c], r[12 + c]);
+                        }
+                        tmem_st4x4_wait(tcol + (uint32_t)(hf * 4), r);
+                        bh = make_float2(fmaf(b0.x, w[8].x, -b0.y * w[8].y),
+                                         fmaf(b0.x, w[8].y, b0.y * w[8].x));
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[it & (kStages - 1)]);
+                }
+                g0 = g1; g1 = g2; b0 = b1;
+            }
+            // ---------------- epilogue of segment g: H[v, k] += (D[k] + D[64 + k]) / scale ----
+            // The scales come from the split pre-pass and H from the previous flush: wait for
+            // the launch before this one (a no-op after the first time).
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            if (g == 0)
+                for (int t = threadIdx.x; t < kNarrowK; t += kProducers) {
+                    const int k = k0 + t;
+                    s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+                }
+            int go = 0;
+            if (ok) {
+                int good = 1;
+                if (lane == 0) {
+                    good = mbar_wait(dfull, g & 1, a.wait_ns) ? 1 : 0;
+                    if (!good) {
+                        atomicExch(a.status, 4u);
+                        s_abort = 1;
+                    }
+                    good = good && !s_abort;
+                }
+                go = __shfl_sync(0xffffffffu, good, 0);
+                ok = go;
+            }
+            epilogue_barrier();   // s_scale written; the tile is free
+            if (go) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+                float2* trow = reinterpret_cast<float2*>(tile + (size_t)row * kNarrowStride);
+                const int c0 = (warp >> 2) * 16;   // this warp's 16 coefficient columns
+                float rh[16], rl[16], ih[16], il[16];
+                tmem_ld16x4(tl + (uint32_t)c0, tl + (uint32_t)(64 + c0), tl + (uint32_t)(128 + c0),
+                            tl + (uint32_t)(192 + c0), rh, rl, ih, il);
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const float s0v = s_scale[c0 + i], s1v = s_scale[c0 + i + 1];
+                    *reinterpret_cast<float4*>(trow + c0 + i) =
+                        make_float4((rh[i] + rl[i]) * s0v, (ih[i] + il[i]) * s0v,
+                                    (rh[i + 1] + rl[i + 1]) * s1v, (ih[i + 1] + il[i + 1]) * s1v);
+                }
+                // D has been read: the next segment's MMAs may overwrite it
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(dfree);
+            }
+            epilogue_barrier();   // the tile is complete
+            if (go) {
+                // warp w updates tile rows w, w + 16, ...; lane l the coefficients l and l + 32;
+                // the H values of four rows are loaded before any is stored
+#pragma unroll
+                for (int i0 = 0; i0 < kNarrowV / kProdWarps; i0 += 4) {
+                    float2 hv[4][2];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int vv = v0 + warp + kProdWarps * (i0 + i);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int k = k0 + hh * 32 + lane;
+                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                                                              : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int vr = warp + kProdWarps * (i0 + i);
+                        const int vv = v0 + vr;
+                        const float2* trow =
+                            reinterpret_cast<const float2*>(tile + (size_t)vr * kNarrowStride);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int kl = hh * 32 + lane;
+                            const int k = k0 + kl;
+                            if (vv < a.S && k < a.K) {
+                                const float2 x = trow[kl];
+                                a.H[(size_t)vv * a.K + k] =
+                                    make_float2(hv[i][hh].x + x.x, hv[i][hh].y + x.y);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == kProdWarps) {
+        // ---------------- B loader (TMA) ----------------
+        if (lane == 0) {
+            // the split coefficients come from the launch before (the split pre-pass)
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
+                                 (size_t)blockIdx.y * T * Tile<64>::kStageBytes;
+            for (int it = 0; it < T; ++it) {
+                const int st = it & (kStages - 1);
+                if (it >= kStages && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
+                    atomicExch(a.status, 2u);
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                mbar_arrive_tx(&full[st], Tile<64>::kStageBytes);
+                tma_load_1d(c_base + (size_t)st * Tile<64>::kStageBytes, src + (size_t)it * Tile<64>::kStageBytes,
+                            Tile<64>::kStageBytes, &full[st]);
+            }
+        }
+    } else {
+        // ---------------- MMA issuer: no division in this loop ----------------
+        if (lane == 0) {
+            const uint32_t id_full = instr_desc(128, 2 * kNarrowK);   // B = [c_hi | c_lo]
+            const uint32_t id_hi = instr_desc(128, kNarrowK);         // B = c_hi
+            const uint64_t dc0 = smem_desc(smem_u32(c_base), 128, 256);
+            const uint32_t d_re = tmem, d_im = tmem + 128u;
+            const int seg = a.seg_stages;
+            int st = 0, seg_left = 0, g = 0;
+            uint32_t ph = 0;
+            for (int it = 0; it < T; ++it) {
+                uint32_t acc = 1u;
+                if (seg_left == 0) {
+                    // a new segment: the epilogue must have read the previous one out of D
+                    if (g > 0 && !mbar_wait(dfree, (uint32_t)(g - 1) & 1u, a.wait_ns)) {
+                        atomicExch(a.status, 5u);
+                        s_abort = 1;
+                        break;
+                    }
+                    seg_left = seg;
+                    acc = 0u;
+                }
+                if (!mbar_wait(&full[st], ph, a.wait_ns)) {
+                    atomicExch(a.status, 3u);
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t dbs = dc0 + (uint64_t)((st * Tile<64>::kStageBytes) >> 4);
+                const uint32_t as = tmem + (uint32_t)(kNarrowColsD + (it & (kSlotsA - 1)) * 128);
+#pragma unroll
+                for (int k2 = 0; k2 < kKSteps; ++k2) {
+                    const uint64_t db = dbs + (uint64_t)((k2 * Tile<64>::kKStepBytes) >> 4);
+                    const uint32_t a0 = as + (uint32_t)(k2 * 32);
+                    const uint32_t ac = k2 == 0 ? acc : 1u;
+                    mma_f16_ts(d_re, a0, db, id_full, ac);           // Re_hi [c_hi | c_lo]
+                    mma_f16_ts(d_im, a0 + 16u, db, id_full, ac);     // Im_hi [c_hi | c_lo]
+                    mma_f16_ts(d_re, a0 + 8u, db, id_hi, 1u);        // Re_lo c_hi
+                    mma_f16_ts(d_im, a0 + 24u, db, id_hi, 1u);       // Im_lo c_hi
+                }
+                mma_commit(&empty[st]);   // frees the stage (A and B) once these MMAs have read it
+                if (--seg_left == 0 || it + 1 == T) {
+                    mma_commit(dfull);
+                    ++g;
+                    seg_left = 0;
+                }
+                st = (st + 1) & (kStages - 1);
+                ph ^= (st == 0) ? 1u : 0u;
+            }
+            // teardown: every MMA issued above completes before TMEM is freed
+            mma_commit(fin);
+            if (!mbar_wait(fin, 0, a.wait_ns)) atomicExch(a.status, 6u);
+        }
+    }
+
+    // column maxima for the next flush: reset by the producer warps, which have passed
+    // griddepcontrol.wait, i.e. after the split pre-pass has read them
+    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < kProdWarps)
+        for (int t = threadIdx.x; t < a.K; t += kProducers) a.colmax[t] = 0u;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == kProdWarps + 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
 // Splits the staged FP32 coefficients into FP16 hi/lo parts with a power-of-two scale per column
 // and writes them as the B operand of accumulate_tc_kernel<NT>, K-major core matrices:
 //   [k-tile of NT][K-step of 16 frames][row group][core matrix b/8 % 2][row % 8][b % 8]
@@ -577,9 +958,10 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
         // group record: first scan index, and whether the 16 frames are consecutive positions
         // of one scan row (frames beyond n have zero coefficients: any record serves them)
         const int32_t s0 = idx[b];
-        bool run = s0 >= 0 && (s0 % Sx) + 15 < Sx;
+        const int32_t sx0 = s0 >= 0 ? s0 % Sx : 0;
+        bool run = s0 >= 0 && sx0 + 15 < Sx;
         for (int j = 1; j < 16 && run; ++j) run = idx[b + j] == s0 + j;
-        grp[b >> 4] = make_int2(s0, run ? 1 : 0);
+        grp[b >> 4] = make_int2(s0, (run ? 1 : 0) | (sx0 << 1));
     }
     float cm = (kk < K) ? __uint_as_float(colmax[kk]) : 0.f;
     int e = 0;
@@ -625,7 +1007,7 @@ cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cud
 bool split_path_available() { return true; }
 
 cudaError_t prepare_split_kernels() {
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<64>));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_narrow_kernel));
     if (e == cudaSuccess)
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<128>));
     return e;
@@ -634,7 +1016,7 @@ cudaError_t prepare_split_kernels() {
 // Coefficients per CTA: 64 up to K = 64, else 128.
 int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
 
-size_t split_smem_bytes(int NT) { return NT == 64 ? tc_smem_bytes<64>() : tc_smem_bytes<128>(); }
+size_t split_smem_bytes(int NT) { return NT == 64 ? narrow_smem_bytes() : tc_smem_bytes<128>(); }
 
 // Kernel launches of one flush: the split pre-pass and the accumulation.
 int split_launch_count(int /*n*/, int /*segment*/) { return 2; }
@@ -687,7 +1069,8 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     // tensor memory and reads the phase table meanwhile, and reads the group records, the split
     // coefficients, the scales and H only after griddepcontrol.wait
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
+    cfg.gridDim = NT == 64 ? dim3((P->S + kNarrowV - 1) / kNarrowV, 1)
+                           : dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
     cfg.blockDim = dim3(kThreadsTC, 1, 1);
     cfg.dynamicSmemBytes = split_smem_bytes(NT);
     cfg.stream = st;
@@ -696,7 +1079,7 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = NT == 64 ? cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<64>, a)
+    cudaError_t e = NT == 64 ? cudaLaunchKernelEx(&cfg, accumulate_narrow_kernel, a)
                              : cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<128>, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -42,18 +42,31 @@ static __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) 
     return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false once about wait_ns have passed.  The SM
-// cycle counter (cheap to read) measures the time, converted at the maximum SM clock of 2.07 GHz,
-// so at lower clocks the limit is proportionally longer.  The counter is read only after a
-// first burst of polls, so waits that complete quickly never touch it.
+// One try_wait with a suspend-time hint: the thread sleeps until the phase completes or about
+// `hint_ns` pass, instead of polling (polling threads take issue slots from the warps that do the
+// work the barrier waits for).
+static __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, unsigned parity, unsigned hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false once about wait_ns have passed.  Each try
+// sleeps up to 10 us; the SM cycle counter (converted at the maximum SM clock of 2.07 GHz, so at
+// lower clocks the limit is proportionally longer) is checked between tries.
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t wait_ns) {
-    for (int i = 0; i < 64; ++i)
-        if (mbar_try(bar, parity)) return true;
+    if (mbar_try(bar, parity)) return true;
     const long long limit = (long long)(wait_ns * 2.07);
     const long long t0 = clock64();
-    for (unsigned i = 1; i != 0; ++i) {   // also capped at 2^32 polls
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 63u) == 0u && clock64() - t0 > limit) return false;
+    for (unsigned i = 1; i != 0; ++i) {   // also capped at 2^32 tries
+        if (mbar_try_sleep(bar, parity, 10000u)) return true;
+        if (clock64() - t0 > limit) return false;
     }
     return false;
 }
