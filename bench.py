@@ -36,7 +36,7 @@ METRIC = "live WDD frames/s and p99 frame latency vs plain FP32 path; % tensor p
 UNIT = "frames/s"
 LATENCY_SNAPSHOT_EVERY = 1024
 ACCUM_DEPTH = 4096     # frames staged per tensor-core accumulation on the optimised path
-COALESCE = 1024        # pushes gathered into projection launches of up to 1024 frames
+COALESCE = 4096        # pushes gathered into projection launches of up to 4096 frames
 TIMING_REPLAYS = 3     # replays of the step captured with stage-timing events
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 EXEC_FACTOR = 3        # tensor-core products per algorithmic product on the split path
@@ -537,7 +537,7 @@ def main(argv=None) -> int:
     # the plain path: FP32 SIMT, every push accumulated at once, eager launches
     plain = mk("fp32", 0, False)
     # the optimised path: tensor-core split accumulation over ACCUM_DEPTH staged frames,
-    # consecutive pushes overlapped and gathered into 1024-frame projection launches (the
+    # consecutive pushes overlapped and gathered into 4096-frame projection launches (the
     # frames are resident for the whole step)
     opt = mk(path, ACCUM_DEPTH, True, coalesce=COALESCE)
 
@@ -681,7 +681,8 @@ def main(argv=None) -> int:
 
     # ---- roofline of the dominant kernel --------------------------------------------------
     peaks = _peaks()
-    proj_kernel = "project_tc_kernel" if opt.info()["proj_tensor"] else "project_kernel"
+    proj_kernel = {1: "project_tc_kernel", 3: "project_rows_kernel"}.get(
+        opt.info()["proj_engine"], "project_kernel")
     K = rc["rank_k"]
     Sf = acq.scan_y * acq.scan_x               # scan frequencies
     stage_ms = {k: v[0] for k, v in st.items()}

@@ -92,7 +92,7 @@ typedef struct {
     int32_t basis;            /* wdd_basis                                                     */
     int32_t precision;        /* wdd_precision                                                 */
     int32_t frame_dtype;      /* wdd_frame_dtype                                               */
-    int32_t max_batch;        /* most frames per internal launch (at most 1024); larger pushes
+    int32_t max_batch;        /* most frames per internal launch (at most 4096); larger pushes
                                  are split                                                     */
     int32_t accum_depth;      /* frames staged before the phase accumulation runs; 0 = every
                                  push is accumulated at once (the plain path)                  */
@@ -114,8 +114,8 @@ typedef struct {
                                  3.2e-7 at 256 frames, 7.6e-7 at 1024, 3.8e-6 at 4096 on a
                                  128x128 scan); longer segments run slightly faster.  0 = 1024. */
     int32_t accum_mode;       /* wdd_accum_mode: how staged frames are added into H            */
-    int32_t coalesce_frames;  /* tensor-core projection: device or pinned-host pushes are gathered
-                                 until this many frames are pending (at most 1024, from at most 16
+    int32_t coalesce_frames;  /* tensor-core and streaming projections: device or pinned-host pushes are gathered
+                                 until this many frames are pending (at most 4096, from at most 64
                                  pushes) and projected in one launch.  The caller must then keep a
                                  push's frames unchanged until the plan's next wdd_flush,
                                  wdd_snapshot, wdd_finalize, wdd_reset or wdd_set_stream, or until
@@ -126,7 +126,27 @@ typedef struct {
                                  the probe by (q_y cos - q_x sin, q_y sin + q_x cos) on the
                                  detector, so +pi/2 matches detector images turned a quarter
                                  turn as numpy's rot90 over the detector axes does.  0 = aligned. */
+    int32_t proj_engine;      /* wdd_proj_engine: which kernel projects the frames (SPLIT plans;
+                                 FP32 plans always use WDD_PROJ_SIMT)                          */
 } wdd_params;
+
+/* Projection kernels (wdd_params.proj_engine, reported in wdd_plan_info.proj_engine).
+ *  AUTO    SPLIT plans: STREAM where it applies, else TENSOR, else SIMT; FP32 plans: SIMT.
+ *  TENSOR  T = I Bx on the tensor cores with FP16 hi/lo splits of frame and basis, then
+ *          By^T T on the SIMT cores (real basis, uint16/float32 frames, det_x a multiple of
+ *          16).
+ *  SIMT    FP32 on the SIMT cores, frames staged in shared memory (any basis and frame type).
+ *  STREAM  FP32 on the SIMT cores, each thread streaming four detector columns down the rows
+ *          with coalesced loads (real basis with at most 16 functions per axis, uint16/float32
+ *          frames, det_x a multiple of 4 up to 512): the projection reads each frame byte once
+ *          and does about 2 L_y flops per byte, so it is bound by the frame read.  A requested
+ *          engine that does not apply falls back as AUTO does. */
+typedef enum {
+    WDD_PROJ_AUTO = 0,
+    WDD_PROJ_TENSOR = 1,
+    WDD_PROJ_SIMT = 2,
+    WDD_PROJ_STREAM = 3
+} wdd_proj_engine;
 
 /* Fills *p with defaults: FP32, HG_TENSOR, F32 frames, max_batch 256, accum_depth 0, centre at
  * N/2, relative epsilon 1e-3, no overlap across pushes, accum_segment 0 (1024), no scan
@@ -229,12 +249,11 @@ typedef struct {
     int64_t kernel_launches; /* hot-path kernel launches since the plan was created          */
     int32_t staged;          /* frames projected but not yet accumulated                     */
     int32_t finished;
-    int32_t proj_tensor;     /* 1: frames are projected on the tensor cores (split precision,
-                                real basis, uint16/float32 frames, det_x a multiple of 16);
-                                0: on the SIMT cores in FP32                                  */
+    int32_t proj_tensor;     /* 1: frames are projected on the tensor cores (proj_engine
+                                TENSOR); 0: on the SIMT cores in FP32                         */
     int32_t accum_mode;      /* wdd_accum_mode of the plan                                   */
     int32_t pending;         /* frames gathered for a projection launch (coalesce_frames)    */
-    int32_t reserved0;
+    int32_t proj_engine;     /* wdd_proj_engine the plan projects with (never AUTO)          */
 } wdd_plan_info;
 
 /* Reports the plan's derived constants and counters (host-side, no GPU work). */

@@ -90,6 +90,7 @@ cudaError_t prepare_kernels() {
     static cudaError_t status = [] {
         cudaError_t e = prepare_project_kernels();
         if (e == cudaSuccess) e = prepare_project_tc_kernels();
+        if (e == cudaSuccess) e = prepare_project_rows_kernels();
         if (e == cudaSuccess) e = prepare_rows_kernels();
         if (e == cudaSuccess) e = prepare_reconstruct_kernels();
         if (e == cudaSuccess) e = prepare_split_kernels();
@@ -172,6 +173,8 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += (int64_t)P->depth_pad / 2;                         // 16-frame group records
     if (P->proj_tc)                                                          // basis image, By
         b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx) + 4LL * ((P->Ny * P->Ly + 3) / 4 * 4);
+    if (P->proj_rows)                                                        // By, Bx (FP32)
+        b += 4LL * ((P->Ny * P->Ly + 3) / 4 * 4) + 4LL * P->Nx * P->Lx;
     if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) {                            // row slots, G
         const int64_t R = rows_slots(P->Sy, P->depth_pad);
         b += 8LL * R * P->Sx * P->K + 12LL * R + 4LL * P->depth_pad + 4;
@@ -225,6 +228,9 @@ wdd_status launch_pending(wdd_plan* P) {
     float* c_out = P->d_cstage + (size_t)q.slot0 * P->K;
     int32_t* i_out = P->d_idxstage + q.slot0;
     cudaError_t e = staged_launch(P, WDD_STAGE_PROJECT, 1, [&] {
+        if (P->proj_rows)
+            return launch_project_rows(P, q.segs, P->p.frame_dtype, q.n, P->p.overlap_pushes != 0,
+                                       q.ids, c_out, i_out, P->stream);
         return launch_project_tc(P, q.segs, P->p.frame_dtype, q.n, P->p.overlap_pushes != 0, q.ids,
                                  c_out, i_out, P->stream);
     });
@@ -367,9 +373,11 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
     if (p.accum_mode != WDD_ACCUM_DIRECT && p.accum_mode != WDD_ACCUM_SEPARABLE)
         return fail(WDD_ERR_INVALID_ARG, "unknown accumulation mode");
     if (p.coalesce_frames < 0 || p.coalesce_frames > kLaunchFrames)
-        return fail(WDD_ERR_INVALID_ARG, "coalesce_frames must be in [0, 1024]");
+        return fail(WDD_ERR_INVALID_ARG, "coalesce_frames must be in [0, 4096]");
     if (!std::isfinite(p.scan_rotation_rad))
         return fail(WDD_ERR_INVALID_ARG, "scan_rotation_rad must be finite");
+    if (p.proj_engine < WDD_PROJ_AUTO || p.proj_engine > WDD_PROJ_STREAM)
+        return fail(WDD_ERR_INVALID_ARG, "unknown projection engine");
     if (p.precision == WDD_PREC_SPLIT && !split_path_available())
         return fail(WDD_ERR_UNSUPPORTED, "split-precision tensor-core path not built");
 
@@ -465,11 +473,20 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
             delete P;
             return fail(WDD_ERR_UNSUPPORTED, "detector width times basis order too large");
         }
-        // split precision projects on the tensor cores wherever that kernel applies
-        P->proj_tc = (p.precision == WDD_PREC_SPLIT &&
-                      proj_tc_supported(P->Nx, P->Lx, P->complex_basis, p.frame_dtype) &&
-                      proj_tc_smem_bytes(P->Ny, P->Nx, P->Ly, P->Lx, P->K) + 1024 <= lim)
-                         ? 1 : 0;
+        // split precision: the streaming FP32 projection wherever it applies (unless the tensor
+        // cores or the staged SIMT kernel were asked for), else the tensor cores where they
+        // apply, else the staged SIMT kernel; FP32 plans keep the staged SIMT kernel
+        const bool split = p.precision == WDD_PREC_SPLIT;
+        const bool rows_ok = split &&
+                             proj_rows_supported(P->Ny, P->Nx, P->Ly, P->Lx, P->K,
+                                                 P->complex_basis, p.frame_dtype);
+        const bool tc_ok = split && proj_tc_supported(P->Nx, P->Lx, P->complex_basis, p.frame_dtype) &&
+                           proj_tc_smem_bytes(P->Ny, P->Nx, P->Ly, P->Lx, P->K) + 1024 <= lim;
+        const int want = p.proj_engine;
+        if (want == WDD_PROJ_TENSOR && tc_ok) P->proj_tc = 1;
+        else if (want == WDD_PROJ_SIMT && split) P->proj_tc = 0;
+        else if (rows_ok) P->proj_rows = 1;
+        else if (tc_ok) P->proj_tc = 1;
     }
     if (P->K > 4096) {
         delete P;
@@ -542,6 +559,10 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         WDD_ALLOC(P->d_bimg, proj_tc_bimg_halves(P->Nx, P->Lx));
         WDD_ALLOC(P->d_Byre, ((size_t)P->Ny * P->Ly + 3) / 4 * 4);
     }
+    if (P->proj_rows) {
+        WDD_ALLOC(P->d_Byre, ((size_t)P->Ny * P->Ly + 3) / 4 * 4);
+        WDD_ALLOC(P->d_Bxre, (size_t)P->Nx * P->Lx);
+    }
     if (p.accum_mode == WDD_ACCUM_SEPARABLE) {
         const int R = rows_slots(P->Sy, P->depth_pad);
         WDD_ALLOC(P->d_G, (size_t)R * P->Sx * P->K);
@@ -584,6 +605,11 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
             std::vector<float> re((by.size() + 3) / 4 * 4, 0.f);
             for (size_t i = 0; i < by.size(); ++i) re[i] = (float)by[i].x;
             if ((e = cudaMemcpy(P->d_Byre, re.data(), 4 * re.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+        }
+        if (P->d_Bxre) {
+            std::vector<float> re(bx.size());
+            for (size_t i = 0; i < bx.size(); ++i) re[i] = (float)bx[i].x;
+            if ((e = cudaMemcpy(P->d_Bxre, re.data(), 4 * re.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
         }
     }
 
@@ -705,7 +731,7 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
         wdd_status ss = switch_stream(P, st);
         if (ss != WDD_OK) return ss;
     }
-    const bool coalesce = P->p.coalesce_frames > 0 && P->proj_tc && !pageable &&
+    const bool coalesce = P->p.coalesce_frames > 0 && (P->proj_tc || P->proj_rows) && !pageable &&
                           (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     if (coalesce) {
         // gather into the pending launch (at most kLaunchFrames frames from kMaxSegs pushes,
@@ -774,12 +800,15 @@ wdd_status wdd_push_frames(wdd_plan* P, const void* frames, const int32_t* scan_
             // after all earlier work on the stream), or when the caller allowed overlap across
             // pushes
             const bool overlap = off > 0 || flushed || P->p.overlap_pushes != 0;
-            if (P->proj_tc && (reinterpret_cast<uintptr_t>(fsrc) & 15u) == 0) {
+            if ((P->proj_tc || P->proj_rows) && (reinterpret_cast<uintptr_t>(fsrc) & 15u) == 0) {
                 wdd::FrameSegs one{};
                 one.ptr[0] = fsrc;
                 one.first[0] = 0;
                 one.first[1] = nb;
                 one.nseg = 1;
+                if (P->proj_rows)
+                    return launch_project_rows(P, one, P->p.frame_dtype, nb, overlap, ids, c_out,
+                                               i_out, st);
                 return launch_project_tc(P, one, P->p.frame_dtype, nb, overlap, ids, c_out, i_out,
                                          st);
             }
@@ -855,9 +884,9 @@ wdd_status wdd_plan_get_info(const wdd_plan* P, wdd_plan_info* out) {
     out->staged = P->staged;
     out->finished = P->finished ? 1 : 0;
     out->proj_tensor = P->proj_tc;
+    out->proj_engine = P->proj_tc ? WDD_PROJ_TENSOR : P->proj_rows ? WDD_PROJ_STREAM : WDD_PROJ_SIMT;
     out->accum_mode = P->p.accum_mode;
     out->pending = P->pend.n;
-    out->reserved0 = 0;
     return WDD_OK;
 }
 

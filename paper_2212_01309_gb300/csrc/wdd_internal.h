@@ -31,13 +31,13 @@ struct ProjGeom {
     int use_tma;                // 1: device frames copied by cp.async.bulk
 };
 // Frames per projection launch; their scan indices travel as a kernel parameter block.
-constexpr int kLaunchFrames = 1024;
+constexpr int kLaunchFrames = 4096;
 struct IndexBlock {
     int32_t s[kLaunchFrames];
 };
 // Frames of one tensor-core projection launch, possibly from several pushes: CTA b projects
 // frame b - first[j] of segment j, where first[j] <= b < first[j + 1].
-constexpr int kMaxSegs = 16;
+constexpr int kMaxSegs = 64;
 struct FrameSegs {
     const void* ptr[kMaxSegs];
     int32_t first[kMaxSegs + 1];
@@ -105,7 +105,8 @@ struct wdd_plan {
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
-    float* d_Byre = nullptr;       // tensor-core projection: real parts of By, [Ny * Ly] padded to 4
+    float* d_Byre = nullptr;       // tensor-core and streaming projections: real parts of By, [Ny * Ly] padded to 4
+    float* d_Bxre = nullptr;       // streaming projection: real parts of Bx, [Nx * Lx]
     // SEPARABLE accumulation: per-flush row slots and row DFTs
     float2* d_G = nullptr;          // [slots][Sx][K]
     int32_t* d_slotrow = nullptr;   // [slots] scan row of each slot
@@ -114,6 +115,7 @@ struct wdd_plan {
     int32_t* d_frameslot = nullptr; // [depth_pad] slot of each staged frame
     int32_t* d_nslots = nullptr;    // [1] slots in use
     int proj_tc = 0;               // 1: projection on the tensor cores
+    int proj_rows = 0;             // 1: streaming FP32 projection (wdd_project_rows.cu)
     int depth_pad = 0;             // staging depth rounded up to the split kernel's 64-frame stage
     int segment = 1024;            // split path: frames per TMEM accumulation segment
     wdd::PendingLaunch pend;       // pushes gathered for one projection launch
@@ -190,6 +192,13 @@ cudaError_t launch_build_bimg(const wdd_plan* P, uint16_t* img, cudaStream_t st)
 cudaError_t launch_project_tc(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
                               bool overlap, const IndexBlock& idx, float* c_out, int32_t* idx_out,
                               cudaStream_t st);
+// Streaming FP32 projection (real basis, L_y <= 16, uint16/float32 frames, N_x % 4 == 0).
+bool proj_rows_supported(int Ny, int Nx, int Ly, int Lx, int K, int complex_basis, int frame_dtype);
+size_t proj_rows_smem_bytes(int Ny, int Nx, int Ly, int Lx, int K);
+cudaError_t prepare_project_rows_kernels();
+cudaError_t launch_project_rows(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
+                                bool overlap, const IndexBlock& idx, float* c_out,
+                                int32_t* idx_out, cudaStream_t st);
 // Row-factorised accumulation (SEPARABLE mode).
 int rows_slots(int Sy, int depth_pad);   // slots a flush of depth_pad frames can need
 cudaError_t prepare_rows_kernels();

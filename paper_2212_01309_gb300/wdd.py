@@ -23,6 +23,7 @@ BASIS = {"fourier_full": 0, "hg_tensor": 1, "hg_energy": 2}
 PRECISION = {"fp32": 0, "split": 1}
 FRAME_DTYPE = {"u16": 0, "f32": 1, "f64": 2}
 ACCUM_MODE = {"direct": 0, "separable": 1}
+PROJ_ENGINE = {"auto": 0, "tensor": 1, "simt": 2, "stream": 3}
 ARRAY = {"weights": 0, "chi": 1, "accum": 2, "coeff": 3, "spectrum": 4, "basis_y": 5,
          "basis_x": 6, "mask": 7, "coeff_index": 8}
 
@@ -58,6 +59,7 @@ class Params(ctypes.Structure):
         ("accum_segment", ctypes.c_int32),
         ("accum_mode", ctypes.c_int32), ("coalesce_frames", ctypes.c_int32),
         ("scan_rotation_rad", ctypes.c_double),
+        ("proj_engine", ctypes.c_int32),
     ]
 
 
@@ -76,7 +78,7 @@ class PlanInfo(ctypes.Structure):
         ("positions_covered", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("staged", ctypes.c_int32), ("finished", ctypes.c_int32),
         ("proj_tensor", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
-        ("pending", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("pending", ctypes.c_int32), ("proj_engine", ctypes.c_int32),
     ]
 
 
@@ -172,7 +174,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
                 det_center_y=-1.0, det_center_x=-1.0, eps_absolute=False,
                 hbm_budget_bytes=0, proj_cluster=0, overlap_pushes=False,
                 accum_segment=0, accum_mode="direct", coalesce_frames=0,
-                scan_rotation_rad=0.0) -> Params:
+                scan_rotation_rad=0.0, proj_engine="auto") -> Params:
     p = Params()
     _check(lib().wdd_params_default(ctypes.byref(p)), "wdd_params_default")
     p.scan_y, p.scan_x, p.scan_step_m = scan_y, scan_x, scan_step_m
@@ -192,6 +194,7 @@ def make_params(*, scan_y, scan_x, scan_step_m, det_y, det_x, det_px_inv_m, volt
     p.accum_mode = ACCUM_MODE[accum_mode] if isinstance(accum_mode, str) else int(accum_mode)
     p.coalesce_frames = coalesce_frames
     p.scan_rotation_rad = scan_rotation_rad
+    p.proj_engine = PROJ_ENGINE[proj_engine] if isinstance(proj_engine, str) else int(proj_engine)
     return p
 
 

@@ -103,7 +103,7 @@ def test_c2_bench_configuration(torch_cuda, c2_reference, variant):
                 g.snapshot(obj, phase, stream=stream)
             torch.cuda.synchronize()
         else:
-            assert g.info()["proj_tensor"] == 1
+            assert g.info()["proj_engine"] == wdd.PROJ_ENGINE["stream"]
             _graph_step(torch, g, d, idx, B, stream, obj, phase)
         g.check_device()
         info = g.info()

@@ -1,4 +1,5 @@
-"""Projection on the tensor cores (split precision) against the FP64 oracle's projection.
+"""Projection on the tensor cores (split precision, proj_engine "tensor") against the FP64
+oracle's projection.
 
 The tensor-core projection splits the frame and the basis into FP16 hi and lo parts (uint16
 counts exactly), so its coefficients carry FP32-level error: each is held to 2e-6 relative L2
@@ -52,7 +53,7 @@ def test_tensor_projection_matches_oracle(torch_cuda, case, source):
     idx = synth.raster_indices(acq)
     ref = W.coefficients(F, W.build_plan(oracle_params(acq, basis, k)))
     with gpu_plan(acq, basis, k, precision="split", max_batch=len(idx),
-                  accum_depth=len(idx)) as g:
+                  accum_depth=len(idx), proj_engine="tensor") as g:
         assert g.info()["proj_tensor"] == 1
         g.push(to_source(F, source), idx)
         g.check_device()
@@ -68,7 +69,7 @@ def test_sources_give_identical_coefficients(torch_cuda):
     out = []
     for source in ("device", "pinned", "pageable"):
         with gpu_plan(acq, "hg_tensor", 64, precision="split", max_batch=len(idx),
-                      accum_depth=len(idx)) as g:
+                      accum_depth=len(idx), proj_engine="tensor") as g:
             g.push(to_source(F, source), idx)
             g.check_device()
             out.append(g.copy_array("coeff"))
@@ -76,17 +77,26 @@ def test_sources_give_identical_coefficients(torch_cuda):
 
 
 def test_path_selection(torch_cuda):
+    """Split plans project with the streaming FP32 kernel where it applies, on the tensor cores
+    when asked (and applicable); the plain FP32 path keeps the staged SIMT kernel."""
+    from paper_2212_01309_gb300 import wdd
+    E = wdd.PROJ_ENGINE
     a = _acq(128, "u16", 1e4, seed=6)
     with gpu_plan(a, "hg_tensor", 64, precision="split") as g:
-        assert g.info()["proj_tensor"] == 1
+        assert g.info()["proj_engine"] == E["stream"] and g.info()["proj_tensor"] == 0
+    with gpu_plan(a, "hg_tensor", 64, precision="split", proj_engine="tensor") as g:
+        assert g.info()["proj_engine"] == E["tensor"] and g.info()["proj_tensor"] == 1
+    with gpu_plan(a, "hg_tensor", 64, precision="split", proj_engine="simt") as g:
+        assert g.info()["proj_engine"] == E["simt"]
     with gpu_plan(a, "hg_tensor", 64, precision="fp32") as g:
-        assert g.info()["proj_tensor"] == 0          # the plain path stays on the SIMT cores
+        assert g.info()["proj_engine"] == E["simt"]  # the plain path stays on the staged kernel
     b = _acq(40, "u16", 1e4, seed=7)
-    with gpu_plan(b, "hg_tensor", 16, precision="split") as g:
-        assert g.info()["proj_tensor"] == 0          # detector width not a multiple of 16
+    with gpu_plan(b, "hg_tensor", 16, precision="split", proj_engine="tensor") as g:
+        # detector width not a multiple of 16: no tensor-core projection, streaming instead
+        assert g.info()["proj_engine"] == E["stream"]
     c = _acq(32, "f64", None, seed=8)
     with gpu_plan(c, "hg_tensor", 16, precision="split") as g:
-        assert g.info()["proj_tensor"] == 0          # float64 frames
+        assert g.info()["proj_engine"] == E["simt"]  # float64 frames
 
 
 def test_out_of_range_float_frame_is_reported(torch_cuda):
@@ -98,7 +108,8 @@ def test_out_of_range_float_frame_is_reported(torch_cuda):
     idx = synth.raster_indices(acq)
     bad = F[:4].copy()
     bad[2, 10, 20] = 1.0e5
-    with gpu_plan(acq, "hg_tensor", 16, precision="split", max_batch=64) as g:
+    with gpu_plan(acq, "hg_tensor", 16, precision="split", max_batch=64,
+                  proj_engine="tensor") as g:
         g.push(to_source(bad, "device"), idx[:4])
         with pytest.raises(wdd.WddError) as ei:
             g.check_device()
@@ -109,11 +120,11 @@ def test_out_of_range_float_frame_is_reported(torch_cuda):
         g.check_device()
 
 
-def _run(acq, F, idx, pushes, source_of=None, depth=1024, **kw):
+def _run(acq, F, idx, pushes, source_of=None, depth=1024, engine="tensor", **kw):
     # the device copy stays alive for the whole run: gathered pushes are read when launched
     d = to_source(F, "device")
     with gpu_plan(acq, "hg_tensor", 64, precision="split", max_batch=256, accum_depth=depth,
-                  **kw) as g:
+                  proj_engine=engine, **kw) as g:
         pos = 0
         pending_seen = 0
         for i, n in enumerate(pushes):
@@ -126,7 +137,8 @@ def _run(acq, F, idx, pushes, source_of=None, depth=1024, **kw):
         return g.copy_array("accum"), ph.cpu().numpy(), pending_seen
 
 
-def test_coalesced_pushes_match_immediate(torch_cuda):
+@pytest.mark.parametrize("engine", ["tensor", "stream"])
+def test_coalesced_pushes_match_immediate(torch_cuda, engine):
     """Pushes gathered into shared launches (many small ones, more than 16 per launch, some
     crossing the 256-frame launch size) give bit-identical results to projecting every push
     when it is made, as long as the accumulation sees the same groups of frames (one flush at
@@ -141,14 +153,14 @@ def test_coalesced_pushes_match_immediate(torch_cuda):
         n = int(min(left, rng.choice([1, 3, 7, 16, 64, 200, 256])))
         pushes.append(n)
         left -= n
-    H0, ph0, p0 = _run(acq, F, idx, pushes)
-    H1, ph1, p1 = _run(acq, F, idx, pushes, coalesce_frames=256)
+    H0, ph0, p0 = _run(acq, F, idx, pushes, engine=engine)
+    H1, ph1, p1 = _run(acq, F, idx, pushes, engine=engine, coalesce_frames=256)
     assert p0 == 0 and p1 > 0
     assert np.array_equal(H0, H1) and np.array_equal(ph0, ph1)
     # pageable pushes bypass the gathering (and launch what is pending first)
     H2, ph2, _ = _run(acq, F, idx, pushes, source_of=lambda i: "pageable" if i % 3 == 0 else "device",
-                      coalesce_frames=128)
+                      engine=engine, coalesce_frames=128)
     assert np.array_equal(H0, H2) and np.array_equal(ph0, ph2)
-    H3, ph3, _ = _run(acq, F, idx, pushes, depth=300, coalesce_frames=256)
+    H3, ph3, _ = _run(acq, F, idx, pushes, depth=300, engine=engine, coalesce_frames=256)
     assert rel_l2(H3, H0) < 3e-6
     assert W.phase_rel_l2(ph3.astype(np.float64), ph0.astype(np.float64)) < 1e-5
