@@ -274,7 +274,8 @@ def run_serving(args) -> int:
         frames = TorchFrames(acq).all()
         p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
                                         epsilon=rc["epsilon"], precision="split", max_batch=512,
-                                        accum_depth=2048, overlap_pushes=True)
+                                        accum_depth=2048, coalesce_frames=1024,
+                                        overlap_pushes=True)
         sessions.append(serving.Session(sid=sid, params=p, frames=frames, n_frames=acq.n_frames))
         # the plain path for the same session: FP32 SIMT kernels, every push accumulated at once
         q = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
@@ -295,11 +296,15 @@ def run_serving(args) -> int:
                       "precision": "split", "cuda_graph_snapshots": True,
                       "deadline_run_snapshot_max_delay_ms": deadline * 1e3}}
     results = {}
-    runs = [("open_loop", sessions, True, None), ("open_loop_deadline", sessions, True, deadline),
-            ("closed_loop", sessions, False, None), ("closed_loop_fp32_plain", plain, False, None)]
-    for mode, specs, open_loop, delay in runs:
+    runs = [("open_loop", sessions, True, None, False),
+            ("open_loop_deadline", sessions, True, deadline, False),
+            ("open_loop_deadline_grouped", sessions, True, deadline, True),
+            ("closed_loop", sessions, False, None, False),
+            ("closed_loop_grouped", sessions, False, None, True),
+            ("closed_loop_fp32_plain", plain, False, None, False)]
+    for mode, specs, open_loop, delay, grouped in runs:
         srv = serving.Server(hbm_budget_bytes=budget, snapshot_every=1024, use_graphs=True,
-                             snapshot_max_delay_s=delay)
+                             snapshot_max_delay_s=delay, grouped=grouped)
         for s in specs:
             srv.add_session(s)
         setup = srv.admit_now()          # plans (Algorithm 1) built when the sessions are set up
@@ -318,8 +323,9 @@ def run_serving(args) -> int:
         for sid in sorted(results["closed_loop"])]
     out["closed_loop"]["phase_std_per_session"] = [
         float(results["closed_loop"][sid].std()) for sid in sorted(results["closed_loop"])]
-    out["closed_loop"]["speedup_vs_fp32_plain"] = (out["closed_loop"]["frames_per_s"] /
-                                                   out["closed_loop_fp32_plain"]["frames_per_s"])
+    for mode in ("closed_loop", "closed_loop_grouped"):
+        out[mode]["speedup_vs_fp32_plain"] = (out[mode]["frames_per_s"] /
+                                              out["closed_loop_fp32_plain"]["frames_per_s"])
     out["value"] = out["closed_loop"]["frames_per_s"]
     print(json.dumps(out), flush=True)
     return 0
@@ -405,11 +411,14 @@ def serving_slice(seconds=2.0, deadline_s=0.02) -> dict:
     out = {"schedule_s": seconds, "frames": int(sum(need)), "arrival_rate_fps": 20000,
            "snapshot_every": 1024, "deadline_ms": deadline_s * 1e3,
            "sessions": sum(1 for n in need if n)}
-    runs = [("open_loop_deadline", "split", True, deadline_s),
-            ("closed_loop", "split", False, None),
-            ("closed_loop_fp32_plain", "fp32", False, None)]
-    for mode, prec, open_loop, delay in runs:
-        srv = serving.Server(snapshot_every=1024, use_graphs=True, snapshot_max_delay_s=delay)
+    runs = [("open_loop_deadline", "split", True, deadline_s, False),
+            ("open_loop_deadline_grouped", "split", True, deadline_s, True),
+            ("closed_loop", "split", False, None, False),
+            ("closed_loop_grouped", "split", False, None, True),
+            ("closed_loop_fp32_plain", "fp32", False, None, False)]
+    for mode, prec, open_loop, delay, grouped in runs:
+        srv = serving.Server(snapshot_every=1024, use_graphs=True, snapshot_max_delay_s=delay,
+                             grouped=grouped)
         for sp in specs[prec]:
             srv.add_session(sp)
         srv.admit_now()
@@ -419,6 +428,8 @@ def serving_slice(seconds=2.0, deadline_s=0.02) -> dict:
                      "p99_ms": st["latency_p99_ms"], "wall_s": st["wall_s"]}
     out["speedup_vs_fp32_plain"] = (out["closed_loop"]["frames_per_s"] /
                                     out["closed_loop_fp32_plain"]["frames_per_s"])
+    out["grouped_speedup_vs_fp32_plain"] = (out["closed_loop_grouped"]["frames_per_s"] /
+                                            out["closed_loop_fp32_plain"]["frames_per_s"])
     return out
 
 

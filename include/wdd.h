@@ -224,6 +224,29 @@ wdd_status wdd_finalize(wdd_plan* plan, wdd_result* out);
  * launches that can be captured once in a CUDA graph and replayed. */
 wdd_status wdd_flush(wdd_plan* plan);
 
+/* wdd_flush for several plans at once.  The pushes the plans have gathered (coalesce_frames) are
+ * projected (Eq. 12) by shared launches: streaming-projection plans with equal frame type and
+ * basis width share one launch of up to 4096 frames from up to 64 pushes; other plans project
+ * their own.  Then the frames staged by every plan are accumulated (the sum of Eq. 14 over each
+ * plan's frames, Sect. 6.3) by one coefficient-split launch and one tensor-core accumulation
+ * launch whose CTAs cover all the plans' tiles, instead of two launches per plan.  This is how a
+ * server that holds many small sessions keeps the GPU's SMs filled: each session alone stages too
+ * few frames and frequency tiles to occupy them.
+ *  plans   count distinct plans, host array.  Every plan must use precision SPLIT with the
+ *          direct accumulation (accum_mode DIRECT), be unfinished, and belong to the device
+ *          that is current.
+ *  count   1 .. wdd_flush_group_max().
+ *  stream  every plan's stream becomes `stream` (as wdd_set_stream); their gathered pushes are
+ *          projected and the accumulation runs on it.
+ * Plans with nothing staged are skipped.  Each shared launch is counted, and timed when timing
+ * is on, on the first plan it serves.  Results equal those of wdd_flush on each plan.
+ * Errors: INVALID_ARG (NULL or repeated plan, count out of range, a plan not SPLIT/DIRECT;
+ * nothing enqueued), STATE (a plan finalized; nothing enqueued), CUDA. */
+wdd_status wdd_flush_group(wdd_plan* const* plans, int32_t count, wdd_stream_t stream);
+
+/* Most plans one wdd_flush_group call takes. */
+int32_t wdd_flush_group_max(void);
+
 /* Sets the stream on which the plan's next snapshot, finalize or reset is enqueued (pushes set
  * it too).  Work already enqueued on the previous stream is ordered before later work on the
  * new one. */

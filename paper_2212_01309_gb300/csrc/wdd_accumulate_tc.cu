@@ -232,7 +232,7 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float (&o0
 }
 
 template <int NT>
-__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
+__device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int by) {
     using TL = Tile<NT>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int v0 = blockIdx.x * kTileV;
-    const int k0 = blockIdx.y * NT;
+    const int v0 = bx * kTileV;
+    const int k0 = by * NT;
     const int T = a.stages_total;
 
     if (threadIdx.x == 0) {
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
             // the split coefficients come from the launch before (the split pre-pass)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
-                                 (size_t)blockIdx.y * T * TL::kStageBytes;
+                                 (size_t)by * T * TL::kStageBytes;
             for (int it = 0; it < T; ++it) {
                 const int st = it & (kStages - 1);
                 if (it >= kStages && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
 
     // column maxima for the next flush: reset by the producer warps, which have passed
     // griddepcontrol.wait, i.e. after the split pre-pass has read them
-    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < kProdWarps)
+    if (bx == 0 && by == 0 && warp < kProdWarps)
         for (int t = threadIdx.x; t < a.K; t += kProducers) a.colmax[t] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -566,6 +566,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcAr
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
     }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_tc_kernel(const TcArgs a) {
+    accumulate_stacked<NT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---- K <= 64: 128 frequencies x 64 coefficients per CTA ----------------------------------------
@@ -618,7 +623,7 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t t0, uint32_t t1, uint32_t t
     tmem_ld16x2(t2, t3, o2, o3);
 }
 
-__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const TcArgs a) {
+__device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int by) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const TcLayout L = narrow_layout();
@@ -635,8 +640,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const 
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int v0 = blockIdx.x * kNarrowV;
-    const int k0 = blockIdx.y * kNarrowK;
+    const int v0 = bx * kNarrowV;
+    const int k0 = by * kNarrowK;
     const int T = a.stages_total;
 
     if (threadIdx.x == 0) {
@@ -854,7 +859,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const 
             // the split coefficients come from the launch before (the split pre-pass)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             const uint8_t* src = reinterpret_cast<const uint8_t*>(a.csplit) +
-                                 (size_t)blockIdx.y * T * Tile<64>::kStageBytes;
+                                 (size_t)by * T * Tile<64>::kStageBytes;
             for (int it = 0; it < T; ++it) {
                 const int st = it & (kStages - 1);
                 if (it >= kStages && !mbar_wait(&empty[st], ((it >> 2) - 1) & 1, a.wait_ns)) {
@@ -925,7 +930,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const 
 
     // column maxima for the next flush: reset by the producer warps, which have passed
     // griddepcontrol.wait, i.e. after the split pre-pass has read them
-    if (blockIdx.x == 0 && blockIdx.y == 0 && warp < kProdWarps)
+    if (bx == 0 && by == 0 && warp < kProdWarps)
         for (int t = threadIdx.x; t < a.K; t += kProducers) a.colmax[t] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -936,6 +941,40 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const 
     }
 }
 
+__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const TcArgs a) {
+    accumulate_narrow(a, blockIdx.x, blockIdx.y);
+}
+
+// ---- several plans in one launch (wdd_flush_group) -----------------------------------------------
+// The CTAs of plan j are the linear block indices first[j] .. first[j + 1] - 1 (its (v, k) tiles in
+// the order of the single-plan grid, x fastest); each CTA runs exactly the single-plan kernel on
+// its plan's arguments.
+constexpr int kMaxGroup = 8;
+struct TcGroup {
+    TcArgs args[kMaxGroup];
+    int first[kMaxGroup + 1];
+    int xtiles[kMaxGroup];
+    int narrow[kMaxGroup];     // 1: K <= 64 (128-frequency tiles)
+    int n;
+};
+
+__device__ __forceinline__ int group_member(const TcGroup& g, int b) {
+    int j = 0;
+    while (j + 1 < g.n && b >= g.first[j + 1]) ++j;
+    return j;
+}
+
+// One launch for every member: a CTA runs the 128-frequency body for a member with K <= 64 and
+// the stacked body otherwise (both need one CTA per SM and the same warp roles).
+__global__ void __launch_bounds__(kThreadsTC, 1) accumulate_group_kernel(const TcGroup g) {
+    const int j = group_member(g, blockIdx.x);
+    const int local = blockIdx.x - g.first[j];
+    if (g.narrow[j])
+        accumulate_narrow(g.args[j], local % g.xtiles[j], local / g.xtiles[j]);
+    else
+        accumulate_stacked<128>(g.args[j], local % g.xtiles[j], local / g.xtiles[j]);
+}
+
 // Splits the staged FP32 coefficients into FP16 hi/lo parts with a power-of-two scale per column
 // and writes them as the B operand of accumulate_tc_kernel<NT>, K-major core matrices:
 //   [k-tile of NT][K-step of 16 frames][row group][core matrix b/8 % 2][row % 8][b % 8]
@@ -943,14 +982,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_narrow_kernel(const 
 // parts (four consecutive K-steps form a 64-frame stage).  Frames beyond n and coefficients
 // beyond K are zero.  One thread per (frame, column).  The thread of column 0 of every 16th frame
 // also writes that 16-frame group's record.
-__global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* __restrict__ colmax,
-                                   uint16_t* __restrict__ out, float* __restrict__ scale_inv,
-                                   const int32_t* __restrict__ idx, int2* __restrict__ grp,
-                                   int n, int n_pad, int K, int Kp, int NT, int Sx) {
-    // the accumulation launched next sets up meanwhile; it reads this kernel's outputs only after
-    // griddepcontrol.wait.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+struct SplitArgs {
+    const float* c;
+    const unsigned* colmax;
+    uint16_t* out;
+    float* scale_inv;
+    const int32_t* idx;
+    int2* grp;
+    int n, n_pad, K, Kp, NT, Sx;
+};
+
+__device__ __forceinline__ void split_coeff(const SplitArgs& s, int t) {
+    const float* __restrict__ c = s.c;
+    const unsigned* __restrict__ colmax = s.colmax;
+    uint16_t* __restrict__ out = s.out;
+    float* __restrict__ scale_inv = s.scale_inv;
+    const int32_t* __restrict__ idx = s.idx;
+    int2* __restrict__ grp = s.grp;
+    const int n = s.n, n_pad = s.n_pad, K = s.K, Kp = s.Kp, NT = s.NT, Sx = s.Sx;
     const int kk = t % Kp;
     const int b = t / Kp;
     if (b >= n_pad) return;
@@ -982,6 +1031,29 @@ __global__ void split_coeff_kernel(const float* __restrict__ c, const unsigned* 
     out[base + in_lo] = __half_as_ushort(lo);
 }
 
+__global__ void split_coeff_kernel(const SplitArgs s) {
+    // the accumulation launched next sets up meanwhile; it reads this kernel's outputs only after
+    // griddepcontrol.wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    split_coeff(s, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The split pre-pass of several plans: plan j takes threads first[j] .. first[j + 1] - 1.
+struct SplitGroup {
+    SplitArgs args[kMaxGroup];
+    long long first[kMaxGroup + 1];
+    int n;
+};
+
+__global__ void split_coeff_group_kernel(const SplitGroup g) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 0;
+    while (j + 1 < g.n && t >= g.first[j + 1]) ++j;
+    if (t >= g.first[g.n]) return;
+    split_coeff(g.args[j], (int)(t - g.first[j]));
+}
+
 // Exercises the bounded mbarrier wait on a barrier that nothing arrives on: the wait must give
 // up after wait_ns and record code 7 in *status, leaving the context usable.
 __global__ void bounded_wait_selftest_kernel(unsigned* status, uint64_t wait_ns) {
@@ -1010,6 +1082,8 @@ cudaError_t prepare_split_kernels() {
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_narrow_kernel));
     if (e == cudaSuccess)
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<128>));
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_group_kernel));
     return e;
 }
 
@@ -1027,22 +1101,35 @@ size_t split_coeff_bytes(int K, int depth_pad) {
     return (size_t)Kp * depth_pad * 2 * 2;   // hi and lo halves
 }
 
-cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
-                                    cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+namespace {
+
+SplitArgs make_split_args(const wdd_plan* P, const float* c, const int32_t* idx, int n,
+                          long long* threads) {
     const int NT = split_tile_n(P->K);
     const int Kp = (P->K + NT - 1) / NT * NT;
     const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
-    if (n_pad > P->depth_pad) return cudaErrorInvalidValue;
-    // 1. split the coefficients (per-column scale from the projection's running max) and mark
-    //    the 16-frame groups
-    {
-        const size_t total = (size_t)n_pad * Kp;
-        split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-            c, P->d_colmax, reinterpret_cast<uint16_t*>(P->d_bsplit), P->d_scale_inv, idx,
-            P->d_grp, n, n_pad, P->K, Kp, NT, P->Sx);
-    }
-    // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
+    SplitArgs s;
+    s.c = c;
+    s.colmax = P->d_colmax;
+    s.out = reinterpret_cast<uint16_t*>(P->d_bsplit);
+    s.scale_inv = P->d_scale_inv;
+    s.idx = idx;
+    s.grp = P->d_grp;
+    s.n = n;
+    s.n_pad = n_pad;
+    s.K = P->K;
+    s.Kp = Kp;
+    s.NT = NT;
+    s.Sx = P->Sx;
+    *threads = (long long)n_pad * Kp;
+    return s;
+}
+
+// Accumulation arguments of one plan and its grid (x: frequency tiles, y: coefficient tiles).
+TcArgs make_tc_args(const wdd_plan* P, const int32_t* idx, int n, dim3* grid) {
+    const int NT = split_tile_n(P->K);
+    const int Kp = (P->K + NT - 1) / NT * NT;
+    const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
     TcArgs a;
     a.csplit = reinterpret_cast<const uint16_t*>(P->d_bsplit);
     a.scale_inv = P->d_scale_inv;
@@ -1065,22 +1152,83 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     a.wait_ns = kDeviceWaitNs;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
-    // the launch overlaps the split pre-pass (programmatic dependent launch): it allocates
-    // tensor memory and reads the phase table meanwhile, and reads the group records, the split
-    // coefficients, the scales and H only after griddepcontrol.wait
+    *grid = NT == 64 ? dim3((P->S + kNarrowV - 1) / kNarrowV, 1)
+                     : dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
+    return a;
+}
+
+// The accumulation overlaps the split pre-pass (programmatic dependent launch): it allocates
+// tensor memory and reads the phase table meanwhile, and reads the group records, the split
+// coefficients, the scales and H only after griddepcontrol.wait.
+template <typename Kern, typename Arg>
+cudaError_t launch_dependent(Kern kern, const Arg& arg, dim3 grid, size_t smem, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = NT == 64 ? dim3((P->S + kNarrowV - 1) / kNarrowV, 1)
-                           : dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
+    cfg.gridDim = grid;
     cfg.blockDim = dim3(kThreadsTC, 1, 1);
-    cfg.dynamicSmemBytes = split_smem_bytes(NT);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = NT == 64 ? cudaLaunchKernelEx(&cfg, accumulate_narrow_kernel, a)
-                             : cudaLaunchKernelEx(&cfg, accumulate_tc_kernel<128>, a);
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
+}  // namespace
+
+cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
+                                    cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
+    if (n_pad > P->depth_pad) return cudaErrorInvalidValue;
+    // 1. split the coefficients (per-column scale from the projection's running max) and mark
+    //    the 16-frame groups
+    long long total = 0;
+    const SplitArgs sa = make_split_args(P, c, idx, n, &total);
+    split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sa);
+    // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
+    dim3 grid;
+    const TcArgs a = make_tc_args(P, idx, n, &grid);
+    const int NT = split_tile_n(P->K);
+    cudaError_t e = NT == 64
+        ? launch_dependent(accumulate_narrow_kernel, a, grid, split_smem_bytes(64), st)
+        : launch_dependent(accumulate_tc_kernel<128>, a, grid, split_smem_bytes(128), st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+int accumulate_group_max() { return kMaxGroup; }
+
+cudaError_t launch_accumulate_group(wdd_plan* const* plans, int count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (count > kMaxGroup) return cudaErrorInvalidValue;
+    SplitGroup sg{};
+    TcGroup tg{};
+    long long threads = 0;
+    int ctas = 0;
+    for (int j = 0; j < count; ++j) {
+        const wdd_plan* P = plans[j];
+        const int n = P->staged;
+        long long t = 0;
+        sg.args[j] = make_split_args(P, P->d_cstage, P->d_idxstage, n, &t);
+        sg.first[j] = threads;
+        threads += t;
+        dim3 grid;
+        tg.args[j] = make_tc_args(P, P->d_idxstage, n, &grid);
+        tg.first[j] = ctas;
+        tg.xtiles[j] = (int)grid.x;
+        tg.narrow[j] = split_tile_n(P->K) == 64 ? 1 : 0;
+        ctas += (int)(grid.x * grid.y);
+    }
+    sg.first[count] = threads;
+    sg.n = count;
+    tg.first[count] = ctas;
+    tg.n = count;
+    split_coeff_group_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sg);
+    const size_t smem = split_smem_bytes(64) > split_smem_bytes(128) ? split_smem_bytes(64)
+                                                                     : split_smem_bytes(128);
+    cudaError_t e = launch_dependent(accumulate_group_kernel, tg, dim3((unsigned)ctas, 1, 1), smem, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -672,6 +672,80 @@ wdd_status wdd_flush(wdd_plan* P) {
     return flush(P);
 }
 
+int32_t wdd_flush_group_max(void) { return accumulate_group_max(); }
+
+wdd_status wdd_flush_group(wdd_plan* const* plans, int32_t count, wdd_stream_t stream) {
+    if (!plans) return fail(WDD_ERR_INVALID_ARG, "plans is NULL");
+    if (count < 1 || count > accumulate_group_max())
+        return fail(WDD_ERR_INVALID_ARG, "group size out of range");
+    for (int j = 0; j < count; ++j) {
+        const wdd_plan* P = plans[j];
+        if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
+        for (int i = 0; i < j; ++i)
+            if (plans[i] == P) return fail(WDD_ERR_INVALID_ARG, "plan repeated in the group");
+        if (P->p.precision != WDD_PREC_SPLIT || P->p.accum_mode != WDD_ACCUM_DIRECT)
+            return fail(WDD_ERR_INVALID_ARG, "grouped flush needs SPLIT plans with DIRECT accumulation");
+        if (P->finished) return fail(WDD_ERR_STATE, "plan already finalized");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int j = 0; j < count; ++j) {
+        wdd_status ss = switch_stream(plans[j], st);
+        if (ss != WDD_OK) return ss;
+    }
+    // gathered pushes: streaming-projection plans of one class share launches, the others
+    // project their own
+    wdd_plan* rows[wdd::kProjGroupMax];
+    int nr = 0;
+    for (int j = 0; j < count; ++j) {
+        wdd_plan* P = plans[j];
+        if (P->pend.n == 0) continue;
+        if (P->proj_rows && nr < wdd::kProjGroupMax) {
+            rows[nr++] = P;
+        } else {
+            wdd_status ls = launch_pending(P);
+            if (ls != WDD_OK) return ls;
+        }
+    }
+    bool taken[wdd::kProjGroupMax] = {};
+    for (int i = 0; i < nr; ++i) {
+        if (taken[i]) continue;
+        wdd_plan* grp[wdd::kProjGroupMax];
+        int ng = 0, frames = 0, nseg = 0;
+        for (int k = i; k < nr; ++k) {
+            wdd_plan* P = rows[k];
+            if (taken[k] || wdd::proj_rows_class(P) != wdd::proj_rows_class(rows[i])) continue;
+            if (frames + P->pend.n > wdd::kLaunchFrames || nseg + P->pend.segs.nseg > wdd::kMaxSegs)
+                continue;
+            grp[ng++] = P;
+            frames += P->pend.n;
+            nseg += P->pend.segs.nseg;
+            taken[k] = true;
+        }
+        cudaError_t e = staged_launch(grp[0], WDD_STAGE_PROJECT, 1, [&] {
+            return wdd::launch_project_rows_group(grp, ng, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "grouped projection");
+        for (int k = 0; k < ng; ++k) {
+            wdd::PendingLaunch& q = grp[k]->pend;
+            grp[k]->last_coeff_off = q.slot0;
+            grp[k]->last_coeff_n = q.n;
+            q.n = 0;
+            q.segs.nseg = 0;
+        }
+    }
+    wdd_plan* active[64];
+    int m = 0;
+    for (int j = 0; j < count; ++j)
+        if (plans[j]->staged > 0) active[m++] = plans[j];
+    if (m == 0) return WDD_OK;
+    cudaError_t e = staged_launch(active[0], WDD_STAGE_ACCUMULATE, 2, [&] {
+        return launch_accumulate_group(active, m, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "grouped phase accumulation");
+    for (int j = 0; j < m; ++j) active[j]->staged = 0;
+    return WDD_OK;
+}
+
 wdd_status wdd_plan_destroy(wdd_plan* P) {
     if (!P) return fail(WDD_ERR_INVALID_ARG, "plan is NULL");
     if (P->stream) cudaStreamSynchronize(P->stream);

@@ -38,6 +38,8 @@ struct IndexBlock {
 // Frames of one tensor-core projection launch, possibly from several pushes: CTA b projects
 // frame b - first[j] of segment j, where first[j] <= b < first[j + 1].
 constexpr int kMaxSegs = 64;
+// Most plans in one grouped projection launch.
+constexpr int kProjGroupMax = 8;
 struct FrameSegs {
     const void* ptr[kMaxSegs];
     int32_t first[kMaxSegs + 1];
@@ -199,6 +201,12 @@ cudaError_t prepare_project_rows_kernels();
 cudaError_t launch_project_rows(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
                                 bool overlap, const IndexBlock& idx, float* c_out,
                                 int32_t* idx_out, cudaStream_t st);
+// Plans whose gathered pushes may share one grouped projection launch have equal classes.
+int proj_rows_class(const wdd_plan* P);
+// One launch projecting the gathered pushes of several streaming-projection plans of one class
+// (at most kProjGroupMax plans, kLaunchFrames frames and kMaxSegs pushes in all); each plan's
+// coefficients go to its own staging slots.  Leaves the plans' pending lists unchanged.
+cudaError_t launch_project_rows_group(wdd_plan* const* plans, int count, cudaStream_t st);
 // Row-factorised accumulation (SEPARABLE mode).
 int rows_slots(int Sy, int depth_pad);   // slots a flush of depth_pad frames can need
 cudaError_t prepare_rows_kernels();
@@ -216,6 +224,9 @@ int split_launch_count(int n, int segment);       // kernel launches of a flush 
 cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cudaStream_t st);
 cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int32_t* idx, int n,
                                     cudaStream_t st);
+// One split pre-pass and one accumulation launch over the staged frames of several split plans.
+int accumulate_group_max();
+cudaError_t launch_accumulate_group(wdd_plan* const* plans, int count, cudaStream_t st);
 cudaError_t launch_deconvolve(const wdd_plan* P, cudaStream_t st);
 cudaError_t launch_inverse_dft(const wdd_plan* P, float2* obj, float* phase, cudaStream_t st);
 // The normalisation and conjugated inverse DFT of Eq. 3 on any spectrum o [Sy][Sx] (tmp: [S]

@@ -107,22 +107,15 @@ __device__ __forceinline__ void use_batch(const float* sBy, int Ny, int r0, int 
     }
 }
 
+// Projects one frame (this CTA's) and writes its coefficients and scan position as staged frame
+// b of a.c_out / a.idx_out.
 template <typename FT, int LYP>
-__global__ void __launch_bounds__(kRowThreads) project_rows_kernel(const PrArgs a,
-                                                                   const FrameSegs segs,
-                                                                   const IndexBlock ids) {
+__device__ __forceinline__ void project_rows(const PrArgs& a, const FT* frame, int b, int32_t pos) {
     extern __shared__ __align__(16) float smr[];
     float* sBy = smr + pr_by_off();
     float* sBx = smr + pr_bx_off(a.Ny, LYP);
     float* sU = smr + pr_u_off(a.Ny, a.Nx, a.Lx, LYP);
     float* red = smr + pr_red_off(a.Ny, a.Nx, a.Lx, LYP);
-    // the next launch may start now; outputs are written after griddepcontrol.wait below
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
-    const int b = blockIdx.x;
-    int sg = 0;
-    while (sg + 1 < segs.nseg && b >= segs.first[sg + 1]) ++sg;
-    const FT* frame = static_cast<const FT*>(segs.ptr[sg]) + (size_t)(b - segs.first[sg]) * a.Ny * a.Nx;
     const int t = threadIdx.x;
     const int G = a.Nx >> 2;            // column groups
     const int R = kRowThreads / G;      // row phases
@@ -185,7 +178,7 @@ __global__ void __launch_bounds__(kRowThreads) project_rows_kernel(const PrArgs 
     __syncthreads();
     // outputs may alias staging slots the previous kernel still reads: wait for it first
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (t == 0) a.idx_out[b] = ids.s[b];
+    if (t == 0) a.idx_out[b] = pos;
     for (int k = t; k < a.K; k += kRowThreads) {
         float s = 0.f;
         for (int sl = 0; sl < SP; ++sl) s += red[(size_t)sl * a.K + k];
@@ -194,9 +187,65 @@ __global__ void __launch_bounds__(kRowThreads) project_rows_kernel(const PrArgs 
     }
 }
 
+// Segment of CTA b: segs.first[sg] <= b < segs.first[sg + 1].
+__device__ __forceinline__ int frame_segment(const FrameSegs& segs, int b) {
+    int sg = 0;
+    while (sg + 1 < segs.nseg && b >= segs.first[sg + 1]) ++sg;
+    return sg;
+}
+
+template <typename FT, int LYP>
+__global__ void __launch_bounds__(kRowThreads) project_rows_kernel(const PrArgs a,
+                                                                   const FrameSegs segs,
+                                                                   const IndexBlock ids) {
+    // the next launch may start now; outputs are written after griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int b = blockIdx.x;
+    const int sg = frame_segment(segs, b);
+    const FT* frame = static_cast<const FT*>(segs.ptr[sg]) + (size_t)(b - segs.first[sg]) * a.Ny * a.Nx;
+    project_rows<FT, LYP>(a, frame, b, ids.s[b]);
+}
+
+// Several plans' gathered pushes in one launch: CTAs first[j] .. first[j + 1] - 1 project the
+// frames of member j (its own detector size, bases, K and staging slots in args[j]); the frame
+// segments and scan positions of all members follow one another in segs and ids.
+struct PrGroup {
+    PrArgs args[kProjGroupMax];
+    int32_t first[kProjGroupMax + 1];
+    int32_t n;
+};
+
+template <typename FT, int LYP>
+__global__ void __launch_bounds__(kRowThreads) project_rows_group_kernel(const PrGroup g,
+                                                                         const FrameSegs segs,
+                                                                         const IndexBlock ids) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int b = blockIdx.x;
+    int j = 0;
+    while (j + 1 < g.n && b >= g.first[j + 1]) ++j;
+    const PrArgs& a = g.args[j];
+    const int sg = frame_segment(segs, b);
+    const FT* frame = static_cast<const FT*>(segs.ptr[sg]) + (size_t)(b - segs.first[sg]) * a.Ny * a.Nx;
+    project_rows<FT, LYP>(a, frame, b - g.first[j], ids.s[b]);
+}
+
 template <typename FT, int LYP>
 cudaError_t prepare_rows_typed() {
-    return allow_max_dynamic_smem(reinterpret_cast<const void*>(project_rows_kernel<FT, LYP>));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(project_rows_kernel<FT, LYP>));
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(project_rows_group_kernel<FT, LYP>));
+    return e;
+}
+
+template <typename FT>
+cudaError_t launch_rows_group_typed(const PrGroup& g, int LYP, const cudaLaunchConfig_t& cfg,
+                                    const FrameSegs& segs, const IndexBlock& ids) {
+    switch (LYP) {
+        case 4: return cudaLaunchKernelEx(&cfg, project_rows_group_kernel<FT, 4>, g, segs, ids);
+        case 8: return cudaLaunchKernelEx(&cfg, project_rows_group_kernel<FT, 8>, g, segs, ids);
+        case 12: return cudaLaunchKernelEx(&cfg, project_rows_group_kernel<FT, 12>, g, segs, ids);
+        default: return cudaLaunchKernelEx(&cfg, project_rows_group_kernel<FT, 16>, g, segs, ids);
+    }
 }
 
 template <typename FT>
@@ -266,6 +315,62 @@ cudaError_t launch_project_rows(const wdd_plan* P, const FrameSegs& segs, int dt
     cfg.numAttrs = overlap ? 1 : 0;
     if (dtype == WDD_FRAME_U16) return launch_rows_typed<uint16_t>(a, LYP, cfg, segs, ids);
     if (dtype == WDD_FRAME_F32) return launch_rows_typed<float>(a, LYP, cfg, segs, ids);
+    return cudaErrorInvalidValue;
+}
+
+int proj_rows_class(const wdd_plan* P) { return P->p.frame_dtype * 64 + pr_lyp(P->Ly); }
+
+cudaError_t launch_project_rows_group(wdd_plan* const* plans, int count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (count > kProjGroupMax) return cudaErrorInvalidValue;
+    const int cls = proj_rows_class(plans[0]);
+    // the merged segment list and scan positions (kernel parameters, 17 KB: kept off the stack)
+    thread_local FrameSegs segs;
+    thread_local IndexBlock ids;
+    PrGroup g{};
+    int frames = 0, nseg = 0;
+    size_t smem = 0;
+    for (int j = 0; j < count; ++j) {
+        const wdd_plan* P = plans[j];
+        const PendingLaunch& q = P->pend;
+        if (!P->proj_rows || proj_rows_class(P) != cls || q.n <= 0) return cudaErrorInvalidValue;
+        if (frames + q.n > kLaunchFrames || nseg + q.segs.nseg > kMaxSegs) return cudaErrorInvalidValue;
+        PrArgs& a = g.args[j];
+        a.Ny = P->Ny;
+        a.Nx = P->Nx;
+        a.Ly = P->Ly;
+        a.Lx = P->Lx;
+        a.K = P->K;
+        a.By = P->d_Byre;
+        a.Bx = P->d_Bxre;
+        a.ktab = P->d_ktab;
+        a.c_out = P->d_cstage + (size_t)q.slot0 * P->K;
+        a.idx_out = P->d_idxstage + q.slot0;
+        a.colmax = P->d_colmax;
+        g.first[j] = frames;
+        for (int k = 0; k < q.segs.nseg; ++k) {
+            segs.ptr[nseg + k] = q.segs.ptr[k];
+            segs.first[nseg + k] = frames + q.segs.first[k];
+        }
+        for (int b = 0; b < q.n; ++b) ids.s[frames + b] = q.ids.s[b];
+        nseg += q.segs.nseg;
+        frames += q.n;
+        const size_t m = proj_rows_smem_bytes(P->Ny, P->Nx, P->Ly, P->Lx, P->K);
+        if (m > smem) smem = m;
+    }
+    g.first[count] = frames;
+    g.n = count;
+    segs.first[nseg] = frames;
+    segs.nseg = nseg;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)frames, 1, 1);
+    cfg.blockDim = dim3(kRowThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    const int LYP = pr_lyp(plans[0]->Ly);
+    const int dtype = plans[0]->p.frame_dtype;
+    if (dtype == WDD_FRAME_U16) return launch_rows_group_typed<uint16_t>(g, LYP, cfg, segs, ids);
+    if (dtype == WDD_FRAME_F32) return launch_rows_group_typed<float>(g, LYP, cfg, segs, ids);
     return cudaErrorInvalidValue;
 }
 

@@ -14,6 +14,12 @@ batches arrive over time.  The loop:
     snapshot has waited `snapshot_max_delay_s` (a display refresh deadline, optional),
     accumulates the staged frames (wdd_flush) and replays the session's captured CUDA graph of
     the reconstruction (deconvolution and inverse DFT), recording an event;
+  * grouped mode (`grouped=True`): the pushes of every split-precision session only gather
+    frames on one shared stream, and at the end of each pass over the sessions those that reached
+    a snapshot point are flushed together (wdd_flush_group, up to wdd_flush_group_max() plans per
+    call): their gathered frames are projected by shared launches and accumulated by one split
+    launch and one tensor-core launch, after which each session's reconstruction graph replays on
+    its own stream.  Sessions of other precisions keep the per-session flush;
   * measures each frame's latency from its arrival to the completion of the first snapshot that
     contains it.
 
@@ -42,12 +48,22 @@ class Session:
     n_frames: int
 
 
+def _groupable(params: wdd.Params) -> bool:
+    return (params.precision == wdd.PRECISION["split"]
+            and params.accum_mode == wdd.ACCUM_MODE["direct"])
+
+
 class _Live:
-    def __init__(self, spec: Session, use_graph: bool):
+    def __init__(self, spec: Session, use_graph: bool, group_stream=None):
         import torch
         self.spec = spec
         self.plan = wdd.Plan(spec.params)
         self.stream = torch.cuda.Stream()
+        # grouped sessions push on the shared stream; their snapshots replay on their own
+        self.push_stream = group_stream if group_stream is not None else self.stream
+        self.due = False                         # grouped: a snapshot point has been reached
+        self.due_final = False
+        self.recon_done = None                   # event after the last reconstruction
         sy, sx = spec.params.scan_y, spec.params.scan_x
         self.obj = torch.empty((sy, sx), dtype=torch.complex64, device="cuda")
         self.phase = torch.empty((sy, sx), dtype=torch.float32, device="cuda")
@@ -68,6 +84,8 @@ class _Live:
                 self.plan.snapshot(self.obj, self.phase)
                 g.capture_end()
             self.graph = g
+        if self.push_stream is not self.stream:
+            self.plan.set_stream(self.push_stream)
 
     def snapshot(self, final: bool):
         import torch
@@ -83,14 +101,35 @@ class _Live:
         self.unsnapped = []
         self.since_snap = 0
 
+    def reconstruct_after(self, flushed):
+        """Grouped mode: the reconstruction of a session flushed by a group flush, on the
+        session's own stream after the event `flushed` of the shared stream."""
+        import torch
+        self.stream.wait_event(flushed)
+        with torch.cuda.stream(self.stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self.plan.snapshot(self.obj, self.phase, stream=self.stream)
+                self.plan.set_stream(self.push_stream)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        self.recon_done = ev
+        self.inflight.append((ev, self.unsnapped, self.due_final))
+        self.unsnapped = []
+        self.since_snap = 0
+        self.due = False
+
 
 class Server:
     """Serving loop.  `hbm_budget_bytes` bounds the summed plan footprints of admitted sessions."""
 
     def __init__(self, hbm_budget_bytes: int | None = None, snapshot_every: int = 1024,
                  use_graphs: bool = True, clock=time.perf_counter,
-                 snapshot_max_delay_s: float | None = None):
+                 snapshot_max_delay_s: float | None = None, grouped: bool = False):
         self.budget = hbm_budget_bytes
+        self.grouped = grouped
+        self.group_stream = None
         self.snapshot_every = snapshot_every
         self.max_delay = snapshot_max_delay_s
         self.use_graphs = use_graphs
@@ -139,7 +178,13 @@ class Server:
                 self.backlog.pop(spec.sid, None)
                 self.admission_log.append((self.clock(), spec.sid, "reject"))
             elif self.budget is None or self.used + need <= self.budget:
-                lv = _Live(spec, self.use_graphs)
+                gs = None
+                if self.grouped and _groupable(spec.params):
+                    if self.group_stream is None:
+                        import torch
+                        self.group_stream = torch.cuda.Stream()
+                    gs = self.group_stream
+                lv = _Live(spec, self.use_graphs, gs)
                 self.live[spec.sid] = lv
                 self.used += need
                 lv.pending.extend(self.backlog.pop(spec.sid, ()))
@@ -150,7 +195,11 @@ class Server:
 
     def _service(self, lv: _Live) -> int:
         """Pushes the session's contiguous pending batches, cut at its snapshot points, and
-        snapshots every `snapshot_every` frames."""
+        snapshots every `snapshot_every` frames.  A grouped session instead stops at its
+        snapshot point and waits for the group flush at the end of the pass."""
+        grouped = lv.push_stream is not lv.stream
+        if lv.due:
+            return 0
         actions = 0
         while lv.pending and lv.pending[0][1] == lv.pushed:
             run = []                       # contiguous requests: [t_arrival, frames left]
@@ -171,22 +220,61 @@ class Server:
                     if run[i][1] == 0:
                         i += 1
                 idx = np.arange(pos, piece_end, dtype=np.int32)
-                lv.plan.push(lv.spec.frames[pos:piece_end], idx, stream=lv.stream)
+                lv.plan.push(lv.spec.frames[pos:piece_end], idx, stream=lv.push_stream)
                 lv.since_snap += piece_end - pos
                 pos = piece_end
                 actions += 1
                 if lv.since_snap >= self.snapshot_every:
-                    lv.snapshot(final=False)
+                    if not grouped:
+                        lv.snapshot(final=False)
+                        continue
+                    # the rest of the run waits until the group flush has taken this snapshot
+                    lv.due = True
+                    back, p0 = [], pos
+                    for t, c in run[i:]:
+                        if c > 0:
+                            back.append((t, p0, c))
+                            p0 += c
+                    lv.pending.extendleft(reversed(back))
+                    lv.pushed = pos
+                    return actions
             lv.pushed = end
         if lv.pushed == lv.spec.n_frames and not lv.closing:
-            lv.snapshot(final=True)
+            if grouped:
+                lv.due = lv.due_final = True
+            else:
+                lv.snapshot(final=True)
             lv.closing = True
             actions += 1
         elif (self.max_delay is not None and lv.unsnapped and not lv.closing and
               self.clock() - lv.unsnapped[0][0] >= self.max_delay):
-            lv.snapshot(final=False)
+            if grouped:
+                lv.due = True
+            else:
+                lv.snapshot(final=False)
             actions += 1
         return actions
+
+    def _flush_due(self) -> int:
+        """Grouped mode: one wdd_flush_group per wdd_flush_group_max() sessions that reached a
+        snapshot point in this pass, then their reconstructions on their own streams."""
+        import torch
+        due = [lv for lv in self.live.values() if lv.due]
+        if not due:
+            return 0
+        gs = self.group_stream
+        m = wdd.flush_group_max()
+        for a in range(0, len(due), m):
+            chunk = due[a:a + m]
+            for lv in chunk:
+                if lv.recon_done is not None:
+                    gs.wait_event(lv.recon_done)     # the last reconstruction still reads H
+            wdd.flush_group([lv.plan for lv in chunk], gs)
+            flushed = torch.cuda.Event()
+            flushed.record(gs)
+            for lv in chunk:
+                lv.reconstruct_after(flushed)
+        return len(due)
 
     def _harvest(self, lv: _Live) -> bool:
         """Records latencies of completed snapshots; returns True when the session is finished."""
@@ -210,8 +298,11 @@ class Server:
         self._admit()
         actions = 0
         for sid in list(self.live):
+            actions += self._service(self.live[sid])
+        if self.grouped:
+            actions += self._flush_due()
+        for sid in list(self.live):
             lv = self.live[sid]
-            actions += self._service(lv)
             if self._harvest(lv):
                 lv.plan.check_device()
                 self.results[sid] = lv.phase.cpu().numpy()

@@ -95,6 +95,9 @@ _SIGS: dict[str, tuple[Any, list[Any]]] = {
                                        ctypes.c_int64]),
     "wdd_plan_footprint": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64)]),
     "wdd_flush": (ctypes.c_int, [ctypes.c_void_p]),
+    "wdd_flush_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                       ctypes.c_void_p]),
+    "wdd_flush_group_max": (ctypes.c_int32, []),
     "wdd_push_frames": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int64, ctypes.c_void_p]),
     "wdd_snapshot": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Result)]),
@@ -410,6 +413,20 @@ class Plan:
         if which in ("basis_y", "basis_x") and not cplx_basis:
             out = out.real.copy()
         return out
+
+
+def flush_group_max() -> int:
+    """Most plans one flush_group call takes."""
+    return int(lib().wdd_flush_group_max())
+
+
+def flush_group(plans, stream) -> None:
+    """Accumulates the staged frames of several SPLIT plans with one coefficient-split launch and
+    one tensor-core launch on `stream` (which becomes every plan's stream); wdd_flush_group."""
+    plans = list(plans)
+    arr = (ctypes.c_void_p * max(1, len(plans)))(*[g._h.value for g in plans])
+    _check(lib().wdd_flush_group(arr, len(plans), ctypes.c_void_p(int(stream.cuda_stream))),
+           "wdd_flush_group")
 
 
 def selftest_bounded_wait(wait_ns: int = 50_000_000) -> int:
