@@ -173,8 +173,8 @@ int64_t planned_bytes(const wdd_plan* P) {
     b += (int64_t)P->depth_pad / 2;                         // 16-frame group records
     if (P->proj_tc)                                                          // basis image, By
         b += 2LL * (int64_t)proj_tc_bimg_halves(P->Nx, P->Lx) + 4LL * ((P->Ny * P->Ly + 3) / 4 * 4);
-    if (P->proj_rows)                                                        // By, Bx (FP32)
-        b += 4LL * ((P->Ny * P->Ly + 3) / 4 * 4) + 4LL * P->Nx * P->Lx;
+    if (P->proj_rows)                                                        // By, Bx (FP32), table
+        b += 4LL * P->Ny * proj_rows_lyp(P->Ly) + 4LL * P->Nx * proj_rows_lxp(P->Lx) + 4LL * P->K;
     if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) {                            // row slots, G
         const int64_t R = rows_slots(P->Sy, P->depth_pad);
         b += 8LL * R * P->Sx * P->K + 12LL * R + 4LL * P->depth_pad + 4;
@@ -560,8 +560,9 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
         WDD_ALLOC(P->d_Byre, ((size_t)P->Ny * P->Ly + 3) / 4 * 4);
     }
     if (P->proj_rows) {
-        WDD_ALLOC(P->d_Byre, ((size_t)P->Ny * P->Ly + 3) / 4 * 4);
-        WDD_ALLOC(P->d_Bxre, (size_t)P->Nx * P->Lx);
+        WDD_ALLOC(P->d_Byp, (size_t)P->Ny * proj_rows_lyp(P->Ly));
+        WDD_ALLOC(P->d_Bxp, (size_t)P->Nx * proj_rows_lxp(P->Lx));
+        WDD_ALLOC(P->d_kpad, P->K);
     }
     if (p.accum_mode == WDD_ACCUM_SEPARABLE) {
         const int R = rows_slots(P->Sy, P->depth_pad);
@@ -606,10 +607,20 @@ wdd_status plan_create_impl(const wdd_params* prm, wdd_plan** out, int64_t* foot
             for (size_t i = 0; i < by.size(); ++i) re[i] = (float)by[i].x;
             if ((e = cudaMemcpy(P->d_Byre, re.data(), 4 * re.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
         }
-        if (P->d_Bxre) {
-            std::vector<float> re(bx.size());
-            for (size_t i = 0; i < bx.size(); ++i) re[i] = (float)bx[i].x;
-            if ((e = cudaMemcpy(P->d_Bxre, re.data(), 4 * re.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+        if (P->proj_rows) {
+            // real parts, zero-padded to the streaming projection's widths, and each
+            // coefficient's place in a padded LYP x LXP block
+            const int LYP = proj_rows_lyp(P->Ly), LXP = proj_rows_lxp(P->Lx);
+            std::vector<float> yp((size_t)P->Ny * LYP, 0.f), xp((size_t)P->Nx * LXP, 0.f);
+            for (int i = 0; i < P->Ny; ++i)
+                for (int l = 0; l < P->Ly; ++l) yp[(size_t)i * LYP + l] = (float)by[(size_t)i * P->Ly + l].x;
+            for (int i = 0; i < P->Nx; ++i)
+                for (int l = 0; l < P->Lx; ++l) xp[(size_t)i * LXP + l] = (float)bx[(size_t)i * P->Lx + l].x;
+            std::vector<int32_t> kp(P->K);
+            for (int k = 0; k < P->K; ++k) kp[k] = kt[2 * k] / P->Lx * LXP + kt[2 * k] % P->Lx;
+            if ((e = cudaMemcpy(P->d_Byp, yp.data(), 4 * yp.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+            if ((e = cudaMemcpy(P->d_Bxp, xp.data(), 4 * xp.size(), cudaMemcpyHostToDevice))) return cbail(e, "basis copy");
+            if ((e = cudaMemcpy(P->d_kpad, kp.data(), 4 * kp.size(), cudaMemcpyHostToDevice))) return cbail(e, "copy table");
         }
     }
 

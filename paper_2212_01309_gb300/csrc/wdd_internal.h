@@ -107,8 +107,10 @@ struct wdd_plan {
     unsigned* d_colmax = nullptr;  // split path: [K] running max |c| per column (float bits)
     unsigned* d_status = nullptr;  // device error word (bounded waits that gave up)
     uint16_t* d_bimg = nullptr;    // tensor-core projection: FP16 hi/lo basis image (B operand)
-    float* d_Byre = nullptr;       // tensor-core and streaming projections: real parts of By, [Ny * Ly] padded to 4
-    float* d_Bxre = nullptr;       // streaming projection: real parts of Bx, [Nx * Lx]
+    float* d_Byre = nullptr;       // tensor-core projection: real parts of By, [Ny * Ly] padded to 4
+    float* d_Byp = nullptr;        // streaming projection: real parts of By, [Ny][LYP] zero-padded
+    float* d_Bxp = nullptr;        // streaming projection: real parts of Bx, [Nx][LXP] zero-padded
+    int32_t* d_kpad = nullptr;     // streaming projection: ly * LXP + lx of each coefficient
     // SEPARABLE accumulation: per-flush row slots and row DFTs
     float2* d_G = nullptr;          // [slots][Sx][K]
     int32_t* d_slotrow = nullptr;   // [slots] scan row of each slot
@@ -196,7 +198,10 @@ cudaError_t launch_project_tc(const wdd_plan* P, const FrameSegs& segs, int dtyp
                               cudaStream_t st);
 // Streaming FP32 projection (real basis, L_y <= 16, uint16/float32 frames, N_x % 4 == 0).
 bool proj_rows_supported(int Ny, int Nx, int Ly, int Lx, int K, int complex_basis, int frame_dtype);
-size_t proj_rows_smem_bytes(int Ny, int Nx, int Ly, int Lx, int K);
+// Padded basis widths of the streaming projection: By is stored [Ny][proj_rows_lyp(Ly)] and Bx
+// [Nx][proj_rows_lxp(Lx)], zero beyond Ly / Lx.
+int proj_rows_lyp(int Ly);
+int proj_rows_lxp(int Lx);
 cudaError_t prepare_project_rows_kernels();
 cudaError_t launch_project_rows(const wdd_plan* P, const FrameSegs& segs, int dtype, int n,
                                 bool overlap, const IndexBlock& idx, float* c_out,

@@ -103,7 +103,8 @@ def test_grouped_flush_equals_per_plan_flush(torch_cuda, members):
             # one projection launch per class of streaming-projection plans with gathered
             # frames (one per plan for the other engines), then split + accumulation
             rows = [i["proj_engine"] == wdd.PROJ_ENGINE["stream"] for i in infos]
-            classes = {(m[0].dtype, (i["basis_ly"] + 3) // 4)
+            classes = {(m[0].dtype, (i["basis_ly"] + 3) // 4, 8 if i["basis_lx"] <= 8 else 16,
+                        (m[0].det // 4 + 31) // 32)
                        for m, i, r in zip(members, infos, rows) if i["pending"] > 0 and r}
             others = sum(1 for i, r in zip(infos, rows) if i["pending"] > 0 and not r)
             assert sum(rows) >= 3

@@ -3,8 +3,9 @@ applies) against the FP64 oracle's projection.
 
 Every product and sum is FP32 on FP32-rounded bases, so each batch's coefficients are held to
 1e-6 relative L2.  Shapes cover detector widths whose four-column groups fill a warp exactly
-(128, 256), leave lanes of the last row phase idle (48, 96, 144) and sixteen Hermite-Gauss
-functions per axis (the register-heavy instance), with uint16 counts and float32 intensities,
+(128), leave lanes of the warp idle (36, 48, 96), fold two row phases into a warp (64), take
+teams of two and four warps per frame (144, 256, 512) and sixteen Hermite-Gauss functions per
+axis (the register-heavy instance), with uint16 counts and float32 intensities,
 from device, pinned and pageable memory; a float32 value far outside the FP16 range (which the
 tensor-core projection must refuse) is projected like any other.
 """
@@ -44,6 +45,9 @@ CASES = [
     ("f32_n48_counts_energy30", 48, "f32", 5e2, "hg_energy", 30),
     ("u16_n256_hg256", 256, "u16", 1e3, "hg_tensor", 256),
     ("f32_n128_energy128", 128, "f32", 1e4, "hg_energy", 128),
+    ("u16_n36_energy20", 36, "u16", 2e3, "hg_energy", 20),
+    ("u16_n64_hg36", 64, "u16", 1e3, "hg_tensor", 36),
+    ("u16_n512_hg64", 512, "u16", 1e3, "hg_tensor", 64),
 ]
 
 
