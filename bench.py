@@ -731,7 +731,7 @@ def main(argv=None) -> int:
         frames_per_launch = S / max(1, st["project"][1])
         bpl = frames_per_launch * frames_bytes
         ach = bpl / (ms_launch * 1e-3) / 1e9
-        tr = _traffic(proj_kernel)
+        tr = _traffic(f"{proj_kernel}/{acq.dtype}") or _traffic(proj_kernel)
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
                 "frac": ach / peaks["hbm"],
                 "traffic": (tr["bytes_per_launch"] * frames_per_launch / tr["frames_per_launch"])
@@ -765,6 +765,20 @@ def main(argv=None) -> int:
                 "note": f"algorithmic 4 S K flops per frame; the split path executes "
                         f"{EXEC_FACTOR}x that (hi*hi, hi*lo and lo*hi products, Re and Im); "
                         f"peak = measured bf16 dense (FP16 same rate)"}
+    # the projection, whatever the dominant kernel: bytes of the frames one launch reads
+    pj_launches = max(1, st["project"][1])
+    pj_fpl = S / pj_launches
+    pj_ms = st["project"][0] / pj_launches
+    pj_tr = (_traffic(f"{proj_kernel}/{acq.dtype}") or _traffic(proj_kernel)) if path == "split" else None
+    roof_proj = {"bound": "hbm", "kernel": proj_kernel, "launch_ms": pj_ms,
+                 "frames_per_launch": pj_fpl,
+                 "achieved": pj_fpl * frames_bytes / (pj_ms * 1e-3) / 1e9, "peak": peaks["hbm"],
+                 "unit": "GB/s",
+                 "frac": pj_fpl * frames_bytes / (pj_ms * 1e-3) / 1e9 / peaks["hbm"],
+                 "traffic": (pj_tr["bytes_per_launch"] * pj_fpl / pj_tr["frames_per_launch"])
+                            if pj_tr else None,
+                 "note": "algorithmic bytes = the frames one launch reads; duration from CUDA "
+                         "events around each launch"}
 
     # ---- extras of the default line: the accumulation at the serving ranks, a serving slice --
     if default_line and not args.no_extras and rank == 0 and world == 1 and path == "split":
@@ -849,6 +863,7 @@ def main(argv=None) -> int:
             "stage_ms_per_step": stage_ms,
             "roofline": roof,
             "roofline_accumulate": roof_acc,
+            "roofline_project": roof_proj,
             "cpu_baseline": cpu,
             "e2e": {"value": job_throughput(S, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": int(S * frames_bytes + 4 * S),
