@@ -48,6 +48,12 @@
 // 2NT + 64 a + 16 ks, lo part 8 columns further; two frames per column).
 // Every mbarrier wait is bounded; a wait that runs out records an error code in *status, the
 // CTA stops issuing work, waits (bounded) for the MMAs it issued and frees its TMEM.
+// This launch starts while the split pre-pass still runs (programmatic dependent launch), so
+// everything earlier launches wrote (the group records and scan indices, the scales, H) is read
+// after griddepcontrol.wait and through L2 (ld.global.cg), never through the non-coherent L1
+// path: with several plans' work in flight on other streams, L1 lines of the previous flush's
+// records were seen served to a later flush.  Only the phase table, fixed since the plan was
+// built, is read through L1.
 
 #include <cuda_fp16.h>
 
@@ -330,8 +336,8 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                 if (it == 0) {
                     // the records come from the split pre-pass, the launch before this one
                     asm volatile("griddepcontrol.wait;" ::: "memory");
-                    g0 = __ldg(gp);
-                    if (T > 1) g1 = __ldg(gp + kKSteps);
+                    g0 = __ldcg(gp);
+                    if (T > 1) g1 = __ldcg(gp + kKSteps);
                     m0 = phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
                     b0 = __ldg(a.tw + m0);
                 }
@@ -350,7 +356,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                     }
                     b1 = __ldg(a.tw + m1);
                 }
-                if (it + 2 < T) g2 = __ldg(gp + (size_t)(it + 2) * kKSteps);
+                if (it + 2 < T) g2 = __ldcg(gp + (size_t)(it + 2) * kKSteps);
                 if (ok) {
                     int good = 1;
                     if (lane == 0) {
@@ -389,7 +395,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                         const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float2 e = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy,
+                            const float2 e = __ldg(a.tw + phase_index((uint32_t)__ldcg(ip + j), vy,
                                                                       vx, a.mod_y, a.mod_x, Sx, my,
                                                                       mx, lcm));
                             x[j] = imag ? e.y : e.x;
@@ -442,7 +448,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
         // the producers passed griddepcontrol.wait at stage 0).
         for (int t = threadIdx.x; t < NT; t += kProducers) {
             const int k = k0 + t;
-            s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+            s_scale[t] = (k < a.K) ? __ldcg(a.scale_inv + k) : 0.f;
         }
         epilogue_barrier();   // s_scale written
         if (ok) {
@@ -464,7 +470,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const int k = k0 + j * 32 + lane;
-                    hv[i][j] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                    hv[i][j] = (vv < a.S && k < a.K) ? __ldcg(a.H + (size_t)vv * a.K + k)
                                                      : make_float2(0.f, 0.f);
                 }
             }
@@ -708,8 +714,8 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
                 if (it == 0) {
                     // the records come from the split pre-pass, the launch before this one
                     asm volatile("griddepcontrol.wait;" ::: "memory");
-                    g0 = __ldg(gp);
-                    if (T > 1) g1 = __ldg(gp + kKSteps);
+                    g0 = __ldcg(gp);
+                    if (T > 1) g1 = __ldcg(gp + kKSteps);
                     b0 = __ldg(a.tw + phase_index((uint32_t)g0.x, vy, vx, a.mod_y, a.mod_x, Sx,
                                                   my, mx, lcm));
                 }
@@ -720,7 +726,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
                 if (it + 1 < T)
                     b1 = __ldg(a.tw + phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my,
                                                   mx, lcm));
-                if (it + 2 < T) g2 = __ldg(gp + (size_t)(it + 2) * kKSteps);
+                if (it + 2 < T) g2 = __ldcg(gp + (size_t)(it + 2) * kKSteps);
                 if (ok) {
                     int good = 1;
                     if (lane == 0) {
@@ -753,7 +759,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
                             const int32_t* ip = a.idx + (size_t)it * kChunk + ks * 16 + hf * 8;
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                e[j] = __ldg(a.tw + phase_index((uint32_t)__ldg(ip + j), vy, vx,
+                                e[j] = __ldg(a.tw + phase_index((uint32_t)__ldcg(ip + j), vy, vx,
                                                                 a.mod_y, a.mod_x, Sx, my, mx, lcm));
                         }
                         uint32_t r[16];   // parts Re_hi, Re_lo, Im_hi, Im_lo: 4 frame pairs each
@@ -779,7 +785,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
             if (g == 0)
                 for (int t = threadIdx.x; t < kNarrowK; t += kProducers) {
                     const int k = k0 + t;
-                    s_scale[t] = (k < a.K) ? a.scale_inv[k] : 0.f;
+                    s_scale[t] = (k < a.K) ? __ldcg(a.scale_inv + k) : 0.f;
                 }
             int go = 0;
             if (ok) {
@@ -829,7 +835,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             const int k = k0 + hh * 32 + lane;
-                            hv[i][hh] = (vv < a.S && k < a.K) ? a.H[(size_t)vv * a.K + k]
+                            hv[i][hh] = (vv < a.S && k < a.K) ? __ldcg(a.H + (size_t)vv * a.K + k)
                                                               : make_float2(0.f, 0.f);
                         }
                     }

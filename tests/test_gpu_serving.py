@@ -196,3 +196,44 @@ def test_grouped_serving_deadline_open_loop(mix_split):
     p = W.Params.from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"])
     _, ph = W.finalize(W.live_wdd(frames, synth.raster_indices(acq), W.build_plan(p)), p)
     assert phase_err(srv.results[0].astype(np.float64), ph) <= 2e-3
+
+
+@pytest.fixture(scope="module")
+def mix_full():
+    """The full serving mix (217,088 uint16 frames, 8.6 GB of frames on the device) with the
+    serving benchmark's split-path parameters: overlapped pushes gathered into 1024-frame
+    launches, 2048 staged frames, a flush and snapshot every 1024 frames per session."""
+    import torch
+    from paper_2212_01309_gb300 import serving, wdd
+    from synth.torch_gen import TorchFrames
+    assert torch.cuda.is_available()
+    sessions = []
+    for sid, (acq, rc) in enumerate(synth.serving_mix()):
+        frames = TorchFrames(acq).all()
+        p = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
+                                        epsilon=rc["epsilon"], max_batch=512, accum_depth=2048,
+                                        precision="split", coalesce_frames=1024,
+                                        overlap_pushes=True)
+        sessions.append((acq, rc, serving.Session(sid=sid, params=p, frames=frames,
+                                                  n_frames=acq.n_frames)))
+    torch.cuda.synchronize()
+    arrivals = synth.serving_arrivals([a.n_frames for a, _, _ in sessions])
+    return sessions, arrivals
+
+
+def test_full_mix_split_equals_alone_repeatedly(mix_full):
+    """Six sessions' flushes in flight at once on six streams: every session's result is
+    bit-identical to the same session served alone, in three runs of the mix.  (The accumulation
+    starts while its split pre-pass still runs; reading the pre-pass's outputs through the
+    non-coherent L1 path once gave one session in six a corrupted result in nearly every run.)"""
+    sessions, arrivals = mix_full
+    alone = {}
+    for sid, (acq, rc, s) in enumerate(sessions):
+        own = [(t, s.sid, st, c) for (t, q, st, c) in arrivals if q == sid]
+        srv, _ = _serve([(acq, rc, s)], own, snapshot_every=1024)
+        alone[sid] = srv.results[sid]
+    for run in range(3):
+        srv, stats = _serve(sessions, arrivals, snapshot_every=1024)
+        assert stats["sessions"] == len(sessions)
+        for sid in alone:
+            assert np.array_equal(srv.results[sid], alone[sid]), (run, sid)
