@@ -1,7 +1,7 @@
 """Full-size parity in the launch configuration the benchmark times.
 
 128x128 scan / 128x128 float32 detector, Hermite-Gauss K = 64, 64-frame pushes gathered into
-1024-frame projection launches, 4096 staged frames per tensor-core flush, pushes overlapped,
+4096-frame projection launches, 4096 staged frames per tensor-core flush, pushes overlapped,
 the whole acquisition captured once as a CUDA graph and replayed: the accumulator, the spectrum
 and the phase against the oracle's full FP64 reconstruction of the same frames (the split path is
 held to the FP32 path's phase bound, 1e-5, and 3e-5 on the accumulator).  The same step through
@@ -84,9 +84,9 @@ def test_c2_bench_configuration(torch_cuda, c2_reference, variant):
     B = rc["batch"]
     kw = dict(basis=rc["basis"], rank_k=rc["rank_k"], epsilon=rc["epsilon"], max_batch=B)
     if variant == "split":
-        kw.update(precision="split", accum_depth=4096, overlap_pushes=True, coalesce_frames=1024)
+        kw.update(precision="split", accum_depth=4096, overlap_pushes=True, coalesce_frames=4096)
     elif variant == "separable":
-        kw.update(precision="split", accum_depth=4096, overlap_pushes=True, coalesce_frames=1024,
+        kw.update(precision="split", accum_depth=4096, overlap_pushes=True, coalesce_frames=4096,
                   accum_mode="separable")
     else:
         kw.update(precision="fp32", accum_depth=0)
@@ -130,7 +130,7 @@ def test_c3_sampled_rows(torch_cuda):
     H_ref = W.accumulate(C, idx, p, v_rows=rows)
     prm = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
                                       precision="split", max_batch=B, accum_depth=4096,
-                                      coalesce_frames=1024, overlap_pushes=True)
+                                      coalesce_frames=4096, overlap_pushes=True)
     stream = torch.cuda.Stream()
     with wdd.Plan(prm) as g, torch.cuda.stream(stream):
         for a in range(0, len(idx), B):
@@ -164,7 +164,7 @@ def test_c5_geometry_streamed_from_pinned_host(torch_cuda):
     H_ref = W.accumulate(C, idx, p, v_rows=rows)
     prm = wdd.params_from_acquisition(acq, basis=rc["basis"], rank_k=rc["rank_k"],
                                       precision="split", max_batch=B, accum_depth=4096,
-                                      coalesce_frames=1024, overlap_pushes=True)
+                                      coalesce_frames=4096, overlap_pushes=True)
     stream = torch.cuda.Stream()
     with wdd.Plan(prm) as g, torch.cuda.stream(stream):
         for a in range(0, n, B):
