@@ -332,8 +332,10 @@ wdd_status wdd_selftest_bounded_wait(int64_t wait_ns);
  * bytes) lives in a fixed 8 MiB array compiled into the library, held on every GPU that loads
  * it until the process exits; scans needing more (above about 524,000 positions) are rejected
  * with WDD_ERR_INVALID_ARG before anything is enqueued.
- * The first call on each device resolves the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one array and every call
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of the process; make that first call before any stream capture.
+ * Resetting a device (cudaDeviceReset) after that call is not supported: the kept address would
+ * no longer belong to the new context.  All calls share the one array and every call
  * writes all of the scratch it reads, so nothing needs clearing, but calls whose work may
  * overlap on the GPU (different streams without ordering) race on it.
  * Errors: INVALID_ARG (NULL, sizes, scratch too small), CUDA. */
