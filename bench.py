@@ -42,6 +42,13 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FM
 EXEC_FACTOR = 3        # tensor-core products per algorithmic product on the split path
 
 
+def exec_factor(info) -> float:
+    """Tensor-core products per algorithmic product of a split plan: three (hi*hi, hi*lo,
+    lo*hi) over the scan columns the accumulation computes (S_x / 2 + 1 of S_x; the rest of H
+    follows from its Hermitian symmetry)."""
+    return EXEC_FACTOR * info["spectrum_cols"] / max(1, info["spectrum_cols_total"])
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -342,8 +349,8 @@ def accumulate_by_rank(acq, d_frames, idx, stream, peaks, n_frames=4096, reps=5)
     """The tensor-core accumulation of one flush of n_frames staged frames on this scan at ranks
     K = 64, 128 and 256 (the serving mix's ranks): device time of the flush (split pre-pass and
     accumulation launch, CUDA events around them on the launch stream), algorithmic 4 S K flops
-    per frame and the EXEC_FACTOR x that the split path executes, against the measured bf16
-    dense peak.  Median of `reps` flushes."""
+    per frame and the tensor-core products the split path executes (exec_factor), against the
+    measured bf16 dense peak.  Median of `reps` flushes."""
     from paper_2212_01309_gb300 import wdd
     S = acq.scan_y * acq.scan_x
     out = {}
@@ -354,6 +361,9 @@ def accumulate_by_rank(acq, d_frames, idx, stream, peaks, n_frames=4096, reps=5)
                                         overlap_pushes=True)
         ms = []
         with wdd.Plan(p) as g:
+            info = dict(g.info(), spectrum_cols_total=acq.scan_x)
+            kern = wdd.ACCUM_KERNEL[info["accum_kernel"]]
+            xf = exec_factor(info)
             for r in range(reps + 1):
                 g.reset(stream=stream)
                 for a in range(0, n_frames, 1024):
@@ -367,11 +377,12 @@ def accumulate_by_rank(acq, d_frames, idx, stream, peaks, n_frames=4096, reps=5)
             g.check_device()
         flush_ms = float(np.median(ms))
         alg = 4.0 * S * K * n_frames / (flush_ms * 1e-3) / 1e12
-        out[f"K{K}"] = {"basis": basis, "flush_frames": n_frames, "flush_ms": flush_ms,
-                        "achieved_algorithmic": alg, "achieved_executed": EXEC_FACTOR * alg,
+        out[f"K{K}"] = {"basis": basis, "kernel": kern, "flush_frames": n_frames,
+                        "flush_ms": flush_ms,
+                        "achieved_algorithmic": alg, "achieved_executed": xf * alg,
                         "peak": peaks["bf16"], "unit": "TFLOP/s",
                         "frac_algorithmic": alg / peaks["bf16"],
-                        "frac_executed": EXEC_FACTOR * alg / peaks["bf16"]}
+                        "frac_executed": xf * alg / peaks["bf16"]}
     return out
 
 
@@ -732,8 +743,9 @@ def main(argv=None) -> int:
     # (all TMEM segments of the flush)
     per_flush = 2 if path == "split" else 1
     flush_frames = min(ACCUM_DEPTH, S)
-    acc_kernel = ("accumulate_narrow_kernel" if K <= 64 else "accumulate_tc_kernel") \
-        if path == "split" else "accumulate_fp32_kernel"
+    acc_info = dict(opt.info(), spectrum_cols_total=acq.scan_x)
+    acc_kernel = wdd.ACCUM_KERNEL[acc_info["accum_kernel"]]
+    xf = exec_factor(acc_info) if path == "split" else 1.0
     ms_launch = st[dom][0] / max(1, st[dom][1])
     if dom == "accumulate":
         ms_launch *= per_flush           # one flush of ACCUM_DEPTH frames
@@ -745,13 +757,15 @@ def main(argv=None) -> int:
                     "frac": ach / peaks["bf16"],
                     "traffic": (tr_a["bytes_per_launch"] * flush_frames / tr_a["frames_per_launch"])
                                if tr_a else None,
-                    "achieved_executed": EXEC_FACTOR * ach,
-                    "frac_executed": EXEC_FACTOR * ach / peaks["bf16"],
+                    "achieved_executed": xf * ach,
+                    "frac_executed": xf * ach / peaks["bf16"],
                     "note": f"one flush of {flush_frames} frames (split pre-pass + one "
-                            f"accumulation launch); algorithmic 4*S*K flops per frame; the split "
-                            f"path executes {EXEC_FACTOR}x that (hi*hi, hi*lo, lo*hi of phase "
-                            f"factors and coefficients); peak = {peaks['src']} bf16 dense (fp16 "
-                            f"same rate)"}
+                            f"accumulation launch); algorithmic 4*S*K flops per frame over all S "
+                            f"scan frequencies; the split path executes {xf:.3f}x that (hi*hi, "
+                            f"hi*lo, lo*hi of phase factors and coefficients on the "
+                            f"{acc_info['spectrum_cols']} of {acq.scan_x} scan columns it "
+                            f"computes; the rest of H by Hermitian symmetry); peak = "
+                            f"{peaks['src']} bf16 dense (fp16 same rate)"}
         else:
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_SIMT_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
@@ -782,7 +796,7 @@ def main(argv=None) -> int:
     acc_ms = st["accumulate"][0] / max(1, st["accumulate"][1]) * per_flush   # per flush
     acc_alg = 4.0 * Sf * K * flush_frames / (acc_ms * 1e-3) / 1e12
     acc_peak = peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS
-    acc_x = EXEC_FACTOR if path == "split" else 1
+    acc_x = xf
     tr_acc = _traffic(acc_kernel) if path == "split" else None
     roof_acc = {"bound": "tensor" if path == "split" else "alu",
                 "kernel": f"split_coeff + {acc_kernel} (one flush of {flush_frames} frames)"
@@ -792,9 +806,10 @@ def main(argv=None) -> int:
                 "achieved_algorithmic": acc_alg, "achieved_executed": acc_alg * acc_x,
                 "peak": acc_peak, "unit": "TFLOP/s",
                 "frac_algorithmic": acc_alg / acc_peak, "frac_executed": acc_alg * acc_x / acc_peak,
-                "note": f"algorithmic 4 S K flops per frame; the split path executes "
-                        f"{EXEC_FACTOR}x that (hi*hi, hi*lo and lo*hi products, Re and Im); "
-                        f"peak = measured bf16 dense (FP16 same rate)"}
+                "note": f"algorithmic 4 S K flops per frame over all S scan frequencies; the "
+                        f"split path executes {xf:.3f}x that (hi*hi, hi*lo and lo*hi products, "
+                        f"Re and Im, on the {acc_info['spectrum_cols']} of {acq.scan_x} scan "
+                        f"columns it computes); peak = measured bf16 dense (FP16 same rate)"}
     # the projection, whatever the dominant kernel: bytes of the frames one launch reads
     pj_launches = max(1, st["project"][1])
     pj_fpl = S / pj_launches

@@ -277,7 +277,24 @@ typedef struct {
     int32_t accum_mode;      /* wdd_accum_mode of the plan                                   */
     int32_t pending;         /* frames gathered for a projection launch (coalesce_frames)    */
     int32_t proj_engine;     /* wdd_proj_engine the plan projects with (never AUTO)          */
+    int32_t accum_kernel;    /* wdd_accum_kernel the plan's flushes run                      */
+    int32_t spectrum_cols;   /* scan columns the accumulation computes: S_x / 2 + 1 on the
+                                SPLIT direct path (the rest of H follows from H[-v] =
+                                conj H[v], Eq. 14 with real coefficients, filled before H is
+                                read), else S_x                                              */
 } wdd_plan_info;
+
+/* Accumulation kernels (wdd_plan_info.accum_kernel): FP32 SIMT (FP32 plans), the row-factorised
+ * SIMT kernels (SEPARABLE), and the tensor-core kernels of the SPLIT path: 128 scan frequencies
+ * x 64 coefficients per CTA (K <= 64 on scans large enough to fill the GPU), the stacked kernel
+ * with 128 coefficients per CTA (K > 64), and with 64 (K <= 64 on smaller scans). */
+typedef enum {
+    WDD_ACCUM_KERNEL_FP32 = 0,
+    WDD_ACCUM_KERNEL_SEPARABLE = 1,
+    WDD_ACCUM_KERNEL_NARROW = 2,
+    WDD_ACCUM_KERNEL_STACKED128 = 3,
+    WDD_ACCUM_KERNEL_STACKED64 = 4
+} wdd_accum_kernel;
 
 /* Reports the plan's derived constants and counters (host-side, no GPU work). */
 wdd_status wdd_plan_get_info(const wdd_plan* plan, wdd_plan_info* out);

@@ -55,6 +55,8 @@
 // records were seen served to a later flush.  Only the phase table, fixed since the plan was
 // built, is read through L1.
 
+#include <algorithm>
+
 #include <cuda_fp16.h>
 
 #include "wdd_device.cuh"
@@ -162,15 +164,23 @@ struct TcArgs {
                               // (s0 mod S_x) << 1 | 1 if the 16 are consecutive positions of
                               // one scan row)
     const float2* tw;         // [lcm] exp(-2 pi i m / lcm), FP32 from FP64
-    float2* H;                // [S][K]
+    float2* H;                // [S_y S_x][K]
     unsigned* status;         // error word (0 = ok)
-    int S, K, Sy, Sx, lcm, my, mx;
+    int S, K, Sy, Sx, lcm, my, mx;   // S: frequencies processed, S_y x Sh (rows of the tiles)
+    int Sh;                   // scan columns processed per row: S_x, or S_x / 2 + 1 when the
+                              // rest follow from Hermitian symmetry (mirror_h_kernel)
     int stages_total;         // 64-frame stages of the flush
     int seg_stages;           // stages per TMEM accumulation segment
     int segments;             // ceil(stages_total / seg_stages)
     uint64_t wait_ns;
     FastMod mod_y, mod_x;
 };
+
+// Row of H of processed frequency number r (r = row Sh + column, column < Sh).
+__device__ __forceinline__ size_t h_row(const TcArgs& a, int r) {
+    const int ry = r / a.Sh;
+    return (size_t)ry * a.Sx + (r - ry * a.Sh);
+}
 
 // Shared-memory layout (offsets from a 1024-byte aligned base).
 struct TcLayout {
@@ -294,8 +304,8 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
         const int vi = (quarter & 1) * 32 + lane;       // frequency within the tile
         // Rows beyond S (last tile) generate v = 0; the epilogue never writes them.
         const int v = (v0 + vi < a.S) ? v0 + vi : 0;
-        const uint32_t vy = (uint32_t)(v / a.Sx);
-        const uint32_t vx = (uint32_t)(v % a.Sx);
+        const uint32_t vy = (uint32_t)(v / a.Sh);
+        const uint32_t vx = (uint32_t)(v % a.Sh);
         const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
         const uint32_t lcm = (uint32_t)a.lcm;
         // w_v^j = exp(-2 pi i j vx / Sx), j = 0..8, from the table (index j vx mx mod lcm)
@@ -470,7 +480,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const int k = k0 + j * 32 + lane;
-                    hv[i][j] = (vv < a.S && k < a.K) ? __ldcg(a.H + (size_t)vv * a.K + k)
+                    hv[i][j] = (vv < a.S && k < a.K) ? __ldcg(a.H + h_row(a, vv) * a.K + k)
                                                      : make_float2(0.f, 0.f);
                 }
             }
@@ -485,7 +495,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                     const int kl = j * 32 + lane;
                     const int k = k0 + kl;
                     if (vv < a.S && k < a.K)
-                        a.H[(size_t)vv * a.K + k] =
+                        a.H[h_row(a, vv) * a.K + k] =
                             make_float2(hv[i][j].x + rre[kl], hv[i][j].y + rim[kl]);
                 }
             }
@@ -682,8 +692,8 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
         const int row = quarter * 32 + lane;            // TMEM lane = frequency in the tile
         // Rows beyond S (last tile) generate v = 0; the epilogue never writes them.
         const int v = (v0 + row < a.S) ? v0 + row : 0;
-        const uint32_t vy = (uint32_t)(v / a.Sx);
-        const uint32_t vx = (uint32_t)(v % a.Sx);
+        const uint32_t vy = (uint32_t)(v / a.Sh);
+        const uint32_t vx = (uint32_t)(v % a.Sh);
         const uint32_t Sx = (uint32_t)a.Sx, my = (uint32_t)a.my, mx = (uint32_t)a.mx;
         const uint32_t lcm = (uint32_t)a.lcm;
         // w_v^j = exp(-2 pi i j vx / Sx), j = 0..8, from the table (index j vx mx mod lcm)
@@ -835,7 +845,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             const int k = k0 + hh * 32 + lane;
-                            hv[i][hh] = (vv < a.S && k < a.K) ? __ldcg(a.H + (size_t)vv * a.K + k)
+                            hv[i][hh] = (vv < a.S && k < a.K) ? __ldcg(a.H + h_row(a, vv) * a.K + k)
                                                               : make_float2(0.f, 0.f);
                         }
                     }
@@ -851,7 +861,7 @@ __device__ __forceinline__ void accumulate_narrow(const TcArgs& a, int bx, int b
                             const int k = k0 + kl;
                             if (vv < a.S && k < a.K) {
                                 const float2 x = trow[kl];
-                                a.H[(size_t)vv * a.K + k] =
+                                a.H[h_row(a, vv) * a.K + k] =
                                     make_float2(hv[i][hh].x + x.x, hv[i][hh].y + x.y);
                             }
                         }
@@ -960,7 +970,7 @@ struct TcGroup {
     TcArgs args[kMaxGroup];
     int first[kMaxGroup + 1];
     int xtiles[kMaxGroup];
-    int narrow[kMaxGroup];     // 1: K <= 64 (128-frequency tiles)
+    int kind[kMaxGroup];       // TcKind of each member
     int n;
 };
 
@@ -975,8 +985,10 @@ __device__ __forceinline__ int group_member(const TcGroup& g, int b) {
 __global__ void __launch_bounds__(kThreadsTC, 1) accumulate_group_kernel(const TcGroup g) {
     const int j = group_member(g, blockIdx.x);
     const int local = blockIdx.x - g.first[j];
-    if (g.narrow[j])
+    if (g.kind[j] == 0)
         accumulate_narrow(g.args[j], local % g.xtiles[j], local / g.xtiles[j]);
+    else if (g.kind[j] == 2)
+        accumulate_stacked<64>(g.args[j], local % g.xtiles[j], local / g.xtiles[j]);
     else
         accumulate_stacked<128>(g.args[j], local % g.xtiles[j], local / g.xtiles[j]);
 }
@@ -1089,6 +1101,8 @@ cudaError_t prepare_split_kernels() {
     if (e == cudaSuccess)
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<128>));
     if (e == cudaSuccess)
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_tc_kernel<64>));
+    if (e == cudaSuccess)
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(accumulate_group_kernel));
     return e;
 }
@@ -1096,7 +1110,12 @@ cudaError_t prepare_split_kernels() {
 // Coefficients per CTA: 64 up to K = 64, else 128.
 int split_tile_n(int K) { return K <= 64 ? 64 : 128; }
 
-size_t split_smem_bytes(int NT) { return NT == 64 ? narrow_smem_bytes() : tc_smem_bytes<128>(); }
+size_t split_smem_bytes(int NT) {
+    if (NT != 64) return tc_smem_bytes<128>();
+    return narrow_smem_bytes() > tc_smem_bytes<64>() ? narrow_smem_bytes() : tc_smem_bytes<64>();
+}
+
+int spectrum_cols(int Sx) { return Sx > 2 ? Sx / 2 + 1 : Sx; }
 
 // Kernel launches of one flush: the split pre-pass and the accumulation.
 int split_launch_count(int /*n*/, int /*segment*/) { return 2; }
@@ -1131,8 +1150,24 @@ SplitArgs make_split_args(const wdd_plan* P, const float* c, const int32_t* idx,
     return s;
 }
 
-// Accumulation arguments of one plan and its grid (x: frequency tiles, y: coefficient tiles).
-TcArgs make_tc_args(const wdd_plan* P, const int32_t* idx, int n, dim3* grid) {
+// Accumulation kernels: the 128-frequency kernel (K <= 64), the stacked kernel with 128 or 64
+// coefficients per CTA.
+enum TcKind { kNarrow = 0, kStacked128 = 1, kStacked64 = 2 };
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 148;
+    return sms;
+}
+
+// Accumulation arguments of one plan, its grid (x: frequency tiles, y: coefficient tiles) and
+// kernel.  Only the scan columns 0 .. S_x / 2 are accumulated (the rest follow from Hermitian
+// symmetry, mirror_h_kernel).  For K <= 64 the 128-frequency kernel does the most work per
+// generated phase factor, but when its tiles cannot fill the SMs once the 64-frequency stacked
+// kernel, with twice the CTAs, finishes sooner.
+TcArgs make_tc_args(const wdd_plan* P, const int32_t* idx, int n, dim3* grid, int* kind) {
     const int NT = split_tile_n(P->K);
     const int Kp = (P->K + NT - 1) / NT * NT;
     const int n_pad = (n + kChunk - 1) / kChunk * kChunk;
@@ -1145,7 +1180,8 @@ TcArgs make_tc_args(const wdd_plan* P, const int32_t* idx, int n, dim3* grid) {
     a.tw = P->d_tw;
     a.H = P->d_H;
     a.status = P->d_status;
-    a.S = P->S;
+    a.Sh = spectrum_cols(P->Sx);
+    a.S = P->Sy * a.Sh;
     a.K = P->K;
     a.Sx = P->Sx;
     a.Sy = P->Sy;
@@ -1158,8 +1194,16 @@ TcArgs make_tc_args(const wdd_plan* P, const int32_t* idx, int n, dim3* grid) {
     a.wait_ns = kDeviceWaitNs;
     a.mod_y = make_fastmod((uint32_t)P->Sy);
     a.mod_x = make_fastmod((uint32_t)P->Sx);
-    *grid = NT == 64 ? dim3((P->S + kNarrowV - 1) / kNarrowV, 1)
-                     : dim3((P->S + kTileV - 1) / kTileV, Kp / NT);
+    if (NT != 64) {
+        *kind = kStacked128;
+        *grid = dim3((a.S + kTileV - 1) / kTileV, Kp / NT);
+    } else if ((a.S + kNarrowV - 1) / kNarrowV >= sm_count()) {
+        *kind = kNarrow;
+        *grid = dim3((a.S + kNarrowV - 1) / kNarrowV, 1);
+    } else {
+        *kind = kStacked64;
+        *grid = dim3((a.S + kTileV - 1) / kTileV, 1);
+    }
     return a;
 }
 
@@ -1195,12 +1239,55 @@ cudaError_t launch_accumulate_split(const wdd_plan* P, const float* c, const int
     split_coeff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sa);
     // 2. tensor-core accumulation of every staged frame, in TMEM segments of P->segment frames
     dim3 grid;
-    const TcArgs a = make_tc_args(P, idx, n, &grid);
-    const int NT = split_tile_n(P->K);
-    cudaError_t e = NT == 64
-        ? launch_dependent(accumulate_narrow_kernel, a, grid, split_smem_bytes(64), st)
-        : launch_dependent(accumulate_tc_kernel<128>, a, grid, split_smem_bytes(128), st);
+    int kind = kNarrow;
+    const TcArgs a = make_tc_args(P, idx, n, &grid, &kind);
+    cudaError_t e =
+        kind == kNarrow ? launch_dependent(accumulate_narrow_kernel, a, grid, narrow_smem_bytes(), st)
+        : kind == kStacked64
+            ? launch_dependent(accumulate_tc_kernel<64>, a, grid, tc_smem_bytes<64>(), st)
+            : launch_dependent(accumulate_tc_kernel<128>, a, grid, tc_smem_bytes<128>(), st);
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// H[v] = conj(H[-v]) for the scan columns S_x / 2 + 1 .. S_x - 1, whose mirror columns
+// S_x - v_x lie in the accumulated half: with real coefficients the spectrum of Eq. 14 is
+// Hermitian, H[-v, k] = sum_s conj(E[v, s]) c_s[k] = conj(H[v, k]).
+__global__ void mirror_h_kernel(float2* H, int Sy, int Sx, int Sh, int K) {
+    const int W = Sx - Sh;
+    const long long n = (long long)Sy * W * K;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % K);
+        const long long r = t / K;
+        const int vy = (int)(r / W), vx = Sh + (int)(r % W);
+        const int my = vy == 0 ? 0 : Sy - vy, mx = Sx - vx;
+        const float2 h = __ldcg(H + ((size_t)my * Sx + mx) * K + k);
+        H[((size_t)vy * Sx + vx) * K + k] = make_float2(h.x, -h.y);
+    }
+}
+
+int accum_kernel_of(const wdd_plan* P) {
+    if (P->p.accum_mode == WDD_ACCUM_SEPARABLE) return WDD_ACCUM_KERNEL_SEPARABLE;
+    if (P->p.precision != WDD_PREC_SPLIT) return WDD_ACCUM_KERNEL_FP32;
+    dim3 grid;
+    int kind = kNarrow;
+    (void)make_tc_args(P, nullptr, kChunk, &grid, &kind);
+    return kind == kNarrow ? WDD_ACCUM_KERNEL_NARROW
+           : kind == kStacked64 ? WDD_ACCUM_KERNEL_STACKED64 : WDD_ACCUM_KERNEL_STACKED128;
+}
+
+bool mirror_needed(const wdd_plan* P) {
+    return P->p.precision == WDD_PREC_SPLIT && P->p.accum_mode == WDD_ACCUM_DIRECT &&
+           spectrum_cols(P->Sx) < P->Sx;
+}
+
+cudaError_t launch_mirror_h(const wdd_plan* P, cudaStream_t st) {
+    const int Sh = spectrum_cols(P->Sx);
+    const long long n = (long long)P->Sy * (P->Sx - Sh) * P->K;
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    mirror_h_kernel<<<(unsigned)blocks, 256, 0, st>>>(P->d_H, P->Sy, P->Sx, Sh, P->K);
     return cudaGetLastError();
 }
 
@@ -1221,10 +1308,11 @@ cudaError_t launch_accumulate_group(wdd_plan* const* plans, int count, cudaStrea
         sg.first[j] = threads;
         threads += t;
         dim3 grid;
-        tg.args[j] = make_tc_args(P, P->d_idxstage, n, &grid);
+        int kind = kNarrow;
+        tg.args[j] = make_tc_args(P, P->d_idxstage, n, &grid, &kind);
         tg.first[j] = ctas;
         tg.xtiles[j] = (int)grid.x;
-        tg.narrow[j] = split_tile_n(P->K) == 64 ? 1 : 0;
+        tg.kind[j] = kind;
         ctas += (int)(grid.x * grid.y);
     }
     sg.first[count] = threads;
@@ -1233,7 +1321,7 @@ cudaError_t launch_accumulate_group(wdd_plan* const* plans, int count, cudaStrea
     tg.n = count;
     split_coeff_group_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sg);
     const size_t smem = split_smem_bytes(64) > split_smem_bytes(128) ? split_smem_bytes(64)
-                                                                     : split_smem_bytes(128);
+                                                                     : split_smem_bytes(128);   // every kind fits
     cudaError_t e = launch_dependent(accumulate_group_kernel, tg, dim3((unsigned)ctas, 1, 1), smem, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

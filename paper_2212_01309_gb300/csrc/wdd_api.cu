@@ -289,7 +289,15 @@ wdd_status reconstruct(wdd_plan* P, wdd_result* out) {
     if (!out || !out->obj) return fail(WDD_ERR_INVALID_ARG, "result buffer is NULL");
     wdd_status st = flush(P);
     if (st != WDD_OK) return st;
-    cudaError_t e = staged_launch(P, WDD_STAGE_DECONVOLVE, 1, [&] { return launch_deconvolve(P, P->stream); });
+    // the split path accumulates half the scan columns: the rest of H follows by symmetry
+    const bool mirror = mirror_needed(P);
+    cudaError_t e = staged_launch(P, WDD_STAGE_DECONVOLVE, mirror ? 2 : 1, [&] {
+        if (mirror) {
+            cudaError_t m = launch_mirror_h(P, P->stream);
+            if (m != cudaSuccess) return m;
+        }
+        return launch_deconvolve(P, P->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "deconvolution");
     e = staged_launch(P, WDD_STAGE_IDFT, 2, [&] {
         return launch_inverse_dft(P, static_cast<float2*>(out->obj), out->phase, P->stream);
@@ -972,6 +980,8 @@ wdd_status wdd_plan_get_info(const wdd_plan* P, wdd_plan_info* out) {
     out->proj_engine = P->proj_tc ? WDD_PROJ_TENSOR : P->proj_rows ? WDD_PROJ_STREAM : WDD_PROJ_SIMT;
     out->accum_mode = P->p.accum_mode;
     out->pending = P->pend.n;
+    out->accum_kernel = accum_kernel_of(P);
+    out->spectrum_cols = mirror_needed(P) ? spectrum_cols(P->Sx) : P->Sx;
     return WDD_OK;
 }
 
@@ -1118,6 +1128,7 @@ wdd_status wdd_copy_array(wdd_plan* P, int32_t which, void* dst, int64_t bytes, 
         case WDD_ARRAY_ACCUM: {
             wdd_status s = flush(P);
             if (s != WDD_OK) return s;
+            if (mirror_needed(P)) WDD_CUDA(launch_mirror_h(P, P->stream));
             src = P->d_H; size = 8ull * P->S * P->K; break;
         }
         case WDD_ARRAY_COEFF:

@@ -224,6 +224,12 @@ constexpr uint64_t kDeviceWaitNs = 2000000000ull;
 bool split_path_available();
 int split_tile_n(int K);
 size_t split_smem_bytes(int NT);
+// Scan columns the tensor-core accumulation computes (S_x / 2 + 1 when S_x > 2): the split path
+// accumulates only these and mirrors the rest (H[-v] = conj H[v]) before H is read.
+int spectrum_cols(int Sx);
+bool mirror_needed(const wdd_plan* P);
+int accum_kernel_of(const wdd_plan* P);   // wdd_accum_kernel
+cudaError_t launch_mirror_h(const wdd_plan* P, cudaStream_t st);
 size_t split_coeff_bytes(int K, int depth_pad);   // bytes of the split coefficient operand
 int split_launch_count(int n, int segment);       // kernel launches of a flush of n frames
 cudaError_t launch_bounded_wait_selftest(unsigned* status, uint64_t wait_ns, cudaStream_t st);

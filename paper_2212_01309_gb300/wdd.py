@@ -23,6 +23,8 @@ BASIS = {"fourier_full": 0, "hg_tensor": 1, "hg_energy": 2}
 PRECISION = {"fp32": 0, "split": 1}
 FRAME_DTYPE = {"u16": 0, "f32": 1, "f64": 2}
 ACCUM_MODE = {"direct": 0, "separable": 1}
+ACCUM_KERNEL = {0: "accumulate_fp32_kernel", 1: "rowdft_kernel", 2: "accumulate_narrow_kernel",
+                3: "accumulate_tc_kernel<128>", 4: "accumulate_tc_kernel<64>"}
 PROJ_ENGINE = {"auto": 0, "tensor": 1, "simt": 2, "stream": 3}
 ARRAY = {"weights": 0, "chi": 1, "accum": 2, "coeff": 3, "spectrum": 4, "basis_y": 5,
          "basis_x": 6, "mask": 7, "coeff_index": 8}
@@ -79,6 +81,7 @@ class PlanInfo(ctypes.Structure):
         ("staged", ctypes.c_int32), ("finished", ctypes.c_int32),
         ("proj_tensor", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
         ("pending", ctypes.c_int32), ("proj_engine", ctypes.c_int32),
+        ("accum_kernel", ctypes.c_int32), ("spectrum_cols", ctypes.c_int32),
     ]
 
 
