@@ -136,11 +136,13 @@ typedef struct {
  *          By^T T on the SIMT cores (real basis, uint16/float32 frames, det_x a multiple of
  *          16).
  *  SIMT    FP32 on the SIMT cores, frames staged in shared memory (any basis and frame type).
- *  STREAM  FP32 on the SIMT cores, each thread streaming four detector columns down the rows
- *          with coalesced loads (real basis with at most 16 functions per axis, uint16/float32
- *          frames, det_x a multiple of 4 up to 512): the projection reads each frame byte once
- *          and does about 2 L_y flops per byte, so it is bound by the frame read.  A requested
- *          engine that does not apply falls back as AUTO does. */
+ *  STREAM  FP32 on the SIMT cores, one warp per frame (teams of det_x / 128 warps for wider
+ *          detectors), each lane streaming four detector columns down the rows with coalesced
+ *          loads and the second contraction combined across lanes by shuffles (real basis with
+ *          at most 16 functions per axis and K <= 256, uint16/float32 frames, det_x a multiple
+ *          of 4 from 16 to 512): the projection reads each frame byte once and does about
+ *          2 L_y flops per pixel, so it is bound by the frame read.  A requested engine that
+ *          does not apply falls back as AUTO does. */
 typedef enum {
     WDD_PROJ_AUTO = 0,
     WDD_PROJ_TENSOR = 1,
