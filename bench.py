@@ -56,14 +56,14 @@ def _env_int(name, default):
         return default
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch of a kernel from the committed ncu record, or None when the
-    kernel's source has changed since the capture."""
+def _traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of a kernel on a workload from the committed ncu record, or None
+    when no capture ran on that workload or the kernel's source has changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f).get(kernel)
+            rec = json.load(f).get(f"{kernel}@{workload}")
         if not rec:
             return None
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
@@ -752,7 +752,7 @@ def main(argv=None) -> int:
         flops = 4.0 * Sf * K * flush_frames
         ach = flops / (ms_launch * 1e-3) / 1e12
         if path == "split":
-            tr_a = _traffic(acc_kernel)
+            tr_a = _traffic(acc_kernel, name)
             roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
                     "frac": ach / peaks["bf16"],
                     "traffic": (tr_a["bytes_per_launch"] * flush_frames / tr_a["frames_per_launch"])
@@ -775,7 +775,7 @@ def main(argv=None) -> int:
         frames_per_launch = S / max(1, st["project"][1])
         bpl = frames_per_launch * frames_bytes
         ach = bpl / (ms_launch * 1e-3) / 1e9
-        tr = _traffic(f"{proj_kernel}/{acq.dtype}") or _traffic(proj_kernel)
+        tr = _traffic(proj_kernel, name)
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
                 "frac": ach / peaks["hbm"],
                 "traffic": (tr["bytes_per_launch"] * frames_per_launch / tr["frames_per_launch"])
@@ -797,7 +797,7 @@ def main(argv=None) -> int:
     acc_alg = 4.0 * Sf * K * flush_frames / (acc_ms * 1e-3) / 1e12
     acc_peak = peaks["bf16"] if path == "split" else FP32_SIMT_PEAK_TFLOPS
     acc_x = xf
-    tr_acc = _traffic(acc_kernel) if path == "split" else None
+    tr_acc = _traffic(acc_kernel, name) if path == "split" else None
     roof_acc = {"bound": "tensor" if path == "split" else "alu",
                 "kernel": f"split_coeff + {acc_kernel} (one flush of {flush_frames} frames)"
                 if path == "split" else acc_kernel, "flush_ms": acc_ms,
@@ -814,7 +814,7 @@ def main(argv=None) -> int:
     pj_launches = max(1, st["project"][1])
     pj_fpl = S / pj_launches
     pj_ms = st["project"][0] / pj_launches
-    pj_tr = (_traffic(f"{proj_kernel}/{acq.dtype}") or _traffic(proj_kernel)) if path == "split" else None
+    pj_tr = _traffic(proj_kernel, name) if path == "split" else None
     roof_proj = {"bound": "hbm", "kernel": proj_kernel, "launch_ms": pj_ms,
                  "frames_per_launch": pj_fpl,
                  "achieved": pj_fpl * frames_bytes / (pj_ms * 1e-3) / 1e9, "peak": peaks["hbm"],

@@ -57,12 +57,13 @@ def test_traffic_record_is_dropped_when_the_source_changes(tmp_path, monkeypatch
     (tmp_path / "profiles").mkdir()
     rec = {"source": "k.cu", "sha256": hashlib.sha256(b"kernel v1").hexdigest(),
            "bytes_per_launch": 123}
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k": rec}))
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k@c2": rec}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic("k")["bytes_per_launch"] == 123
-    assert bench._traffic("other") is None
+    assert bench._traffic("k", "c2")["bytes_per_launch"] == 123
+    assert bench._traffic("other", "c2") is None
+    assert bench._traffic("k", "c5") is None     # captured on another workload
     src.write_text("kernel v2")
-    assert bench._traffic("k") is None
+    assert bench._traffic("k", "c2") is None
 
 
 def test_committed_traffic_records_name_existing_sources():
@@ -72,6 +73,8 @@ def test_committed_traffic_records_name_existing_sources():
         if name.startswith("_"):
             continue
         assert os.path.exists(os.path.join(bench.ROOT, rec["source"])), name
+        kernel, _, workload = name.partition("@")
+        assert kernel and workload in bench.WORKLOADS, name
 
 
 def test_whole_job_rate():
