@@ -35,15 +35,15 @@
 // Warp roles (576 threads, one CTA per SM: all 512 TMEM columns):
 //   warps 0-15  producers: warp w fills TMEM lanes 32 (w % 4) .. + 31 for K-step w / 4 of every
 //               64-frame stage; they also run the epilogue (tcgen05.ld -> FP32 running sums
-//               -> shared-memory tiles -> coalesced H += sum / scale);
+//               in shared-memory tiles -> coalesced H += sum / scale);
 //   warp 16     TMA loader of the B operand;
 //   warp 17     TMEM allocation; one elected lane issues tcgen05.mma and the commits.
 // A stage (64 frames, eight MMAs) is filled by the sixteen producer warps and one TMA copy, all
 // arriving on one `full` barrier, and released by one tcgen05.commit on its `empty` barrier.
 // The issue loop has no integer division (a single thread's scalar latency bounded an earlier
 // version of this loop, not the tensor pipe).  Between segments each producer thread adds its
-// row of D (hi and lo columns) into FP32 registers, so the MMAs wait only for that read; H is
-// read and written once per flush.
+// row of D (hi and lo columns) into FP32 running sums in its part of the shared-memory epilogue
+// tile, so the MMAs wait only for that read; H is read and written once per flush.
 // TMEM columns: D 0 .. 2NT-1, four A slots of 64 columns from 2NT (slot a, K-step ks: hi part at
 // 2NT + 64 a + 16 ks, lo part 8 columns further; two frames per column).
 // Every mbarrier wait is bounded; a wait that runs out records an error code in *status, the
@@ -323,11 +323,14 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
         const uint32_t t_lane = tmem + ((uint32_t)(quarter * 32) << 16) +
                                 (uint32_t)(TL::kColsD + ks * 16);
         // running sums of this thread's row (Re or Im of frequency vi) over the segments, for
-        // coefficient columns cbase .. cbase + NT / 4 - 1 of the tile (FP32)
+        // coefficient columns cbase .. cbase + NT / 4 - 1 of the tile (FP32), kept in this
+        // thread's part of the epilogue tile in shared memory: registers held across the stage
+        // loop slow the producers (9-11 % per flush measured against register sums)
         const int cbase = ks * (NT / 4);
-        float sum[NT / 4];
+        float* srow = (imag ? t_im : t_re) + (size_t)vi * (TL::kRowBytes / 4) + cbase;
 #pragma unroll
-        for (int i = 0; i < NT / 4; ++i) sum[i] = 0.f;
+        for (int i = 0; i < NT / 4; i += 4)
+            *reinterpret_cast<float4*>(srow + i) = make_float4(0.f, 0.f, 0.f, 0.f);
         // this warp's 16 frames of stage it form group 4 it + ks; the group records are written
         // by the split pre-pass.  Records run two stages ahead, the table entry of the group's
         // first position one stage ahead.
@@ -445,7 +448,14 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                     float hi[16], lo[16];
                     tmem_ld16x2(tl + (uint32_t)c0, tl + (uint32_t)(NT + c0), hi, lo);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) sum[16 * h + i] += hi[i] + lo[i];
+                    for (int i = 0; i < 16; i += 4) {
+                        float4 q = *reinterpret_cast<float4*>(srow + 16 * h + i);
+                        q.x += hi[i] + lo[i];
+                        q.y += hi[i + 1] + lo[i + 1];
+                        q.z += hi[i + 2] + lo[i + 2];
+                        q.w += hi[i + 3] + lo[i + 3];
+                        *reinterpret_cast<float4*>(srow + 16 * h + i) = q;
+                    }
                 }
                 // D has been read: the next segment's MMAs may overwrite it
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -460,16 +470,7 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
             const int k = k0 + t;
             s_scale[t] = (k < a.K) ? __ldcg(a.scale_inv + k) : 0.f;
         }
-        epilogue_barrier();   // s_scale written
-        if (ok) {
-            float* trow = (imag ? t_im : t_re) + (size_t)vi * (TL::kRowBytes / 4);
-#pragma unroll
-            for (int i = 0; i < NT / 4; i += 4)
-                *reinterpret_cast<float4*>(trow + cbase + i) = make_float4(
-                    sum[i] * s_scale[cbase + i], sum[i + 1] * s_scale[cbase + i + 1],
-                    sum[i + 2] * s_scale[cbase + i + 2], sum[i + 3] * s_scale[cbase + i + 3]);
-        }
-        epilogue_barrier();   // the tiles are complete
+        epilogue_barrier();   // s_scale written, the tiles of running sums complete
         if (ok) {
             // warp w updates rows w, w + 16, w + 32, w + 48; lane l the coefficients l + 32 j
             constexpr int J = NT / 32;
@@ -494,9 +495,11 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                 for (int j = 0; j < J; ++j) {
                     const int kl = j * 32 + lane;
                     const int k = k0 + kl;
+                    // (sum * scale) rounded, then added: no fused multiply-add
                     if (vv < a.S && k < a.K)
                         a.H[h_row(a, vv) * a.K + k] =
-                            make_float2(hv[i][j].x + rre[kl], hv[i][j].y + rim[kl]);
+                            make_float2(__fadd_rn(hv[i][j].x, __fmul_rn(rre[kl], s_scale[kl])),
+                                        __fadd_rn(hv[i][j].y, __fmul_rn(rim[kl], s_scale[kl])));
                 }
             }
         }
