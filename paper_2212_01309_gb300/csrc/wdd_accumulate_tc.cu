@@ -336,8 +336,10 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
         // first position one stage ahead.
         const int2* gp = a.grp + ks;
         // phase-index step between a group and the group 64 positions further along the same
-        // scan row: (64 vx mod Sx) mx mod lcm
+        // scan row: (64 vx mod Sx) mx mod lcm; when those 64 positions wrap into the next scan
+        // row (raster order), the row step vy my is added as well
         const uint32_t d64 = fastmod(64u * vx, a.mod_x) * mx;   // < lcm
+        const uint32_t dmy = vy * my;                           // < lcm (vy < S_y)
         int2 g0 = make_int2(0, 0), g1 = g0;
         uint32_t m0 = 0;
         float2 b0 = make_float2(1.f, 0.f);
@@ -363,6 +365,11 @@ __device__ __forceinline__ void accumulate_stacked(const TcArgs& a, int bx, int 
                 if (it + 1 < T) {
                     if (g1.x == g0.x + 64 && (g1.y >> 1) == (g0.y >> 1) + 64) {
                         m1 = m0 + d64;
+                        if (m1 >= lcm) m1 -= lcm;
+                    } else if (g1.x == g0.x + 64 && (g1.y >> 1) == (g0.y >> 1) + 64 - a.Sx) {
+                        m1 = m0 + d64;
+                        if (m1 >= lcm) m1 -= lcm;
+                        m1 += dmy;
                         if (m1 >= lcm) m1 -= lcm;
                     } else {
                         m1 = phase_index((uint32_t)g1.x, vy, vx, a.mod_y, a.mod_x, Sx, my, mx, lcm);
