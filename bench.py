@@ -17,6 +17,7 @@ collective on the data path); the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -829,6 +830,11 @@ def main(argv=None) -> int:
     if default_line and not args.no_extras and rank == 0 and world == 1 and path == "split":
         with torch.cuda.stream(stream):
             extras["accumulate_by_rank"] = accumulate_by_rank(acq, d_frames, idx, stream, peaks)
+            # the same flushes on a 256x256 scan (the same detector and frames): four times the
+            # scan frequencies, so the accumulation CTAs fill several waves of the SMs
+            acq256 = dataclasses.replace(acq, scan_y=256, scan_x=256, obj_y=512, obj_x=512)
+            extras["accumulate_by_rank_scan256"] = accumulate_by_rank(
+                acq256, d_frames, synth.raster_indices(acq256), stream, peaks)
         extras["serving"] = serving_slice()
 
     # ---- CPU baseline (rank 0, N = 1) -------------------------------------------------------
