@@ -81,3 +81,11 @@ def test_whole_job_rate():
     assert bench.job_throughput(1000, 1, 2.0) == 500000.0
     assert bench.job_throughput(1000, 4, 2.0) == 2000000.0
     assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_exec_factor_counts_the_computed_scan_columns():
+    # three split products (hi*hi, hi*lo, lo*hi) over the S_x / 2 + 1 computed columns
+    assert bench.exec_factor({"spectrum_cols": 65, "spectrum_cols_total": 128}) == 3 * 65 / 128
+    assert bench.exec_factor({"spectrum_cols": 129, "spectrum_cols_total": 256}) == 3 * 129 / 256
+    # every column computed: three products per algorithmic product
+    assert bench.exec_factor({"spectrum_cols": 40, "spectrum_cols_total": 40}) == 3.0
